@@ -1,0 +1,321 @@
+/*
+ * fpt_oracle.c -- plain FP64 CPU oracle for the stochastic-delta-N
+ * first-passage sampler of arXiv:2410.13683.
+ *
+ * TEST INFRASTRUCTURE ONLY. The product library never calls, links or loads
+ * this file; only the test-suite, the smoke check and the benchmark's CPU
+ * baseline leg do. It shares no code, header, table or constant generator with
+ * the CUDA path: everything here is restated from the paper and from the
+ * published definition of the Philox generator.
+ *
+ * What it computes, step by step, in double precision:
+ *   - Euler-Maruyama steps (Eq. 4.1) of the 1-D-noise Langevin system
+ *     (Eq. 4.6) with the importance-sampling bias of Eq. (4.7); the momentum
+ *     drift carries the minus sign of Eqs. (2.21) and (4.1) (Eq. 4.7 drops it,
+ *     read here as a typo);
+ *   - the bias lies along the noise vector (1, tan theta_n): B = alpha S (1, t).
+ *     The per-dimension weights of Eq. (4.8) agree exactly when
+ *     B_pi = tan(theta_n) B_phi (Eq. 4.9 prints the inverse relation);
+ *   - per-step weight increment dA = alpha (alpha dN / 2 + xi sqrt(dN)), the
+ *     one-dimensional form of Eq. (4.5); w = exp(-sum dA), Eq. (4.4);
+ *   - first passage: the first step n >= 1 with phi_n <= phi_end, N = n dN
+ *     (Sec. 4.1);
+ *   - the noise S(phi) and S_pi(phi) = tan(theta_n) S(phi) come from a
+ *     phi-indexed table by linear interpolation (the phi-indexing proposed in
+ *     Sec. 5); outside the table the end values are held.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+ * (seed_lo, seed_hi), counter = (step >> 2, trajectory id, run id, 0); the four
+ * 32-bit words become uniforms u_k = ((r_k >> 8) + 0.5) 2^-24 and two
+ * Box-Muller pairs (z0, z1) <- (u0, u1), (z2, z3) <- (u2, u3); step i uses
+ * z[i & 3].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, written from its published definition.                    */
+/* ------------------------------------------------------------------------ */
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t *hi, uint32_t *lo)
+{
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;   /* round multipliers */
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;   /* Weyl key bumps    */
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(M0, c0, &hi0, &lo0);
+        mulhilo32(M1, c2, &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Four standard normals for steps 4*block .. 4*block+3 of one trajectory. */
+void oracle_normals4(uint64_t seed, uint32_t run_id, uint32_t traj,
+                     uint32_t block, double z[4])
+{
+    uint32_t ctr[4] = {block, traj, run_id, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    double u[4];
+    for (int k = 0; k < 4; ++k)
+        u[k] = ((double)(r[k] >> 8) + 0.5) * (1.0 / 16777216.0);
+    for (int p = 0; p < 2; ++p) {
+        double rad = sqrt(-2.0 * log(u[2 * p]));
+        double ang = 2.0 * OR_PI * u[2 * p + 1];
+        z[2 * p] = rad * cos(ang);
+        z[2 * p + 1] = rad * sin(ang);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model, table and bias descriptions.                                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t kind;        /* 0: piecewise-linear, relative slopes; 1: V0 exp(mu phi) */
+    int32_t pad;
+    double V0, a_plus, a_minus, phi_star, mu;
+    double phi_in, pi_in, phi_end, dN;
+    int64_t max_steps;
+} oracle_model;
+
+typedef struct {
+    int64_t n_points;    /* M >= 2 */
+    double phi_lo, h;    /* grid phi_j = phi_lo + j h */
+    const double *S;     /* S_phiphi(phi_j)                      */
+    const double *T;     /* S_piphi(phi_j) = tan(theta_n) S(phi_j) */
+} oracle_table;
+
+typedef struct {
+    int32_t kind;        /* 0: none, 1: constant amplitude, 2: MLP */
+    int32_t hidden;      /* MLP width (64) */
+    double A;            /* constant amplitude */
+    int64_t segment;     /* MLP: alpha recomputed every `segment` steps */
+    double alpha_max;    /* MLP: |alpha| clamp */
+    int32_t round_bf16;  /* MLP: round operands to bfloat16 as the GPU does */
+    int32_t pad;
+    const double *W1, *b1, *W2, *b2, *W3, *b3;   /* row-major (out, in) */
+    double in_shift[3], in_scale[3];             /* input = (s - shift) * scale */
+} oracle_bias;
+
+/* Slope term V'(phi)/V(phi) of the two potential families. */
+static double dlnV(const oracle_model *m, double phi)
+{
+    if (m->kind == 1)
+        return m->mu;
+    double d = phi - m->phi_star;
+    double a = (phi >= m->phi_star) ? m->a_plus : m->a_minus;
+    return a / (1.0 + a * d);
+}
+
+/* Linear interpolation of the noise table, end values held outside. */
+static void table_lookup(const oracle_table *t, double phi, double *S, double *T)
+{
+    double M1 = (double)(t->n_points - 1);
+    double u = (phi - t->phi_lo) / t->h;
+    if (u < 0.0) u = 0.0;
+    if (u > M1) u = M1;
+    int64_t i = (int64_t)floor(u);
+    if (i > t->n_points - 2) i = t->n_points - 2;
+    double f = u - (double)i;
+    *S = t->S[i] + f * (t->S[i + 1] - t->S[i]);
+    *T = t->T[i] + f * (t->T[i + 1] - t->T[i]);
+}
+
+/* Round a double to the nearest bfloat16 value (ties to even). */
+static double to_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return v;  /* inf / nan */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double silu(double v) { return v / (1.0 + exp(-v)); }
+
+/* MLP outputs (o1, o2) for state (x, pi, N); x = phi - phi_end. */
+void oracle_mlp_forward(const oracle_bias *b, const double s[3], double o[2])
+{
+    int H = b->hidden;
+    double in[3], h1[256], h2[256];
+    for (int k = 0; k < 3; ++k) {
+        in[k] = (s[k] - b->in_shift[k]) * b->in_scale[k];
+        if (b->round_bf16) in[k] = to_bf16(in[k]);
+    }
+    for (int j = 0; j < H; ++j) {
+        double a = b->b1[j];
+        for (int k = 0; k < 3; ++k) a += b->W1[j * 3 + k] * in[k];
+        h1[j] = silu(a);
+        if (b->round_bf16) h1[j] = to_bf16(h1[j]);
+    }
+    for (int j = 0; j < H; ++j) {
+        double a = b->b2[j];
+        for (int k = 0; k < H; ++k) a += b->W2[j * H + k] * h1[k];
+        h2[j] = silu(a);
+        if (b->round_bf16) h2[j] = to_bf16(h2[j]);
+    }
+    for (int j = 0; j < 2; ++j) {
+        double a = b->b3[j];
+        for (int k = 0; k < H; ++k) a += b->W3[j * H + k] * h2[k];
+        o[j] = a;
+    }
+}
+
+/* Bias amplitude from the MLP: projection of (o1, o2) on the noise direction
+ * (1, t)/sqrt(1 + t^2), clamped to |alpha| <= alpha_max. */
+static double mlp_alpha(const oracle_bias *b, const oracle_model *m,
+                        double phi, double pi, int64_t n, double t)
+{
+    double s[3] = {phi - m->phi_end, pi, (double)n * m->dN};
+    double o[2];
+    oracle_mlp_forward(b, s, o);
+    double a = (o[0] + t * o[1]) / sqrt(1.0 + t * t);
+    if (a > b->alpha_max) a = b->alpha_max;
+    if (a < -b->alpha_max) a = -b->alpha_max;
+    return a;
+}
+
+typedef struct {
+    int64_t *nsteps;
+    double *logw;
+    uint8_t *status;     /* 0: passed, 1: capped at max_steps */
+    double *phi_final;
+    double *pi_final;
+    double *xmin_pre;    /* min of phi_n - phi_end over steps 1..n-1 (inf if none) */
+} oracle_out;
+
+/* Optional per-segment record for the learned-bias gradient. */
+typedef struct {
+    int64_t cap;         /* capacity in segments */
+    int64_t *n_seg;      /* out: segments recorded */
+    double *state;       /* [cap][3] (x, pi, N) at the segment start */
+    double *tan_theta;   /* [cap] t at the segment start */
+    double *alpha;       /* [cap] alpha used */
+    double *sum_xi;      /* [cap] sum of xi over the steps of the segment */
+} oracle_segments;
+
+/* One trajectory, plain FP64 Euler-Maruyama. */
+static void one_trajectory(const oracle_model *m, const oracle_table *tab,
+                           const oracle_bias *b, uint64_t seed, uint32_t run_id,
+                           uint32_t traj, int64_t *nsteps, double *logw,
+                           uint8_t *status, double *phi_f, double *pi_f,
+                           double *xmin, oracle_segments *seg)
+{
+    const double dN = m->dN, sdN = sqrt(m->dN);
+    double phi = m->phi_in, pi = m->pi_in, lw = 0.0, xm = INFINITY;
+    double z[4];
+    double alpha = (b->kind == 1) ? b->A : 0.0;
+    int64_t n = 0, ns = 0;
+    int passed = 0;
+    while (n < m->max_steps) {
+        if ((n & 3) == 0)
+            oracle_normals4(seed, run_id, traj, (uint32_t)(n >> 2), z);
+        double xi = z[n & 3];
+        double S, T;
+        table_lookup(tab, phi, &S, &T);
+        if (b->kind == 2 && (n % b->segment) == 0) {
+            double t = (S != 0.0) ? T / S : 0.0;
+            alpha = mlp_alpha(b, m, phi, pi, n, t);
+            if (seg && ns < seg->cap) {
+                seg->state[3 * ns + 0] = phi - m->phi_end;
+                seg->state[3 * ns + 1] = pi;
+                seg->state[3 * ns + 2] = (double)n * dN;
+                seg->tan_theta[ns] = t;
+                seg->alpha[ns] = alpha;
+                seg->sum_xi[ns] = 0.0;
+            }
+            ++ns;
+        }
+        if (b->kind == 2 && seg && ns - 1 < seg->cap)
+            seg->sum_xi[ns - 1] += xi;
+        double drift_pi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi));
+        double phi_new = phi + pi * dN + alpha * S * dN + S * xi * sdN;
+        double pi_new = pi + drift_pi * dN + alpha * T * dN + T * xi * sdN;
+        lw -= alpha * (0.5 * alpha * dN + xi * sdN);
+        phi = phi_new;
+        pi = pi_new;
+        ++n;
+        if (phi <= m->phi_end) { passed = 1; break; }
+        double x = phi - m->phi_end;
+        if (x < xm) xm = x;
+    }
+    *nsteps = n;
+    *logw = lw;
+    *status = passed ? 0 : 1;
+    *phi_f = phi;
+    *pi_f = pi;
+    *xmin = xm;
+    if (seg) *seg->n_seg = ns < seg->cap ? ns : seg->cap;
+}
+
+/* Run trajectories traj0 .. traj0+n-1 of one run. Returns 0 on success. */
+int oracle_run(const oracle_model *m, const oracle_table *tab,
+               const oracle_bias *b, uint64_t seed, uint32_t run_id,
+               int64_t traj0, int64_t n, int threads, oracle_out *out)
+{
+    if (!m || !tab || !b || !out || n < 0 || tab->n_points < 2) return 1;
+    if (traj0 < 0 || traj0 + n > 4294967296LL) return 1;
+    if (b->kind == 2 && (b->segment <= 0 || b->hidden <= 0 || b->hidden > 256)) return 1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        one_trajectory(m, tab, b, seed, run_id, (uint32_t)(traj0 + i),
+                       &out->nsteps[i], &out->logw[i], &out->status[i],
+                       &out->phi_final[i], &out->pi_final[i], &out->xmin_pre[i],
+                       NULL);
+    }
+    return 0;
+}
+
+/* One trajectory with its segment records (learned-bias gradient checks). */
+int oracle_run_segments(const oracle_model *m, const oracle_table *tab,
+                        const oracle_bias *b, uint64_t seed, uint32_t run_id,
+                        int64_t traj, int64_t *nsteps, double *logw,
+                        uint8_t *status, oracle_segments *seg)
+{
+    if (!m || !tab || !b || !seg || b->kind != 2) return 1;
+    double pf, pif, xm;
+    one_trajectory(m, tab, b, seed, run_id, (uint32_t)traj, nsteps, logw, status,
+                   &pf, &pif, &xm, seg);
+    return 0;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

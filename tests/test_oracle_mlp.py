@@ -1,0 +1,94 @@
+"""Pins of the FP64 learned-proposal reference: finite differences and the
+two independent forward implementations (numpy, C)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mlp as M
+from oracle import stepper as S
+from oracle import tables as T
+
+
+def _params(seed=3, out_scale=0.3):
+    return W.mlp_init(seed, out_scale=out_scale)
+
+
+def test_backward_matches_finite_differences():
+    p = _params()
+    s = W.random_states(7, 1)
+    t = np.linspace(-0.2, 0.3, 7)
+    da = np.linspace(-1.0, 1.0, 7)
+    g = M.alpha_grad(p, s, t, 50.0, da)
+    f = lambda q: float(np.sum(da * M.alpha_of(M.forward(q, s)[0], t, 50.0)))
+    rng = np.random.default_rng(0)
+    for k in M.KEYS:
+        for _ in range(4):
+            idx = tuple(rng.integers(0, d) for d in p[k].shape)
+            h = 1e-6
+            q = {kk: v.copy() for kk, v in p.items()}
+            q[k][idx] += h
+            fp = f(q)
+            q[k][idx] -= 2 * h
+            fm = f(q)
+            fd = (fp - fm) / (2 * h)
+            assert abs(fd - g[k][idx]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_c_and_numpy_forward_agree():
+    p = _params()
+    mlp = S.MLPBias(p, segment=64, in_shift=[0.1, -0.2, 0.3], in_scale=[2.0, 0.5, 1.5],
+                    round_bf16=False)
+    for s in W.random_states(5, 2):
+        oc = S.mlp_forward_c(mlp, s)
+        on, _ = M.forward(p, M.normalise(s[None, :], [0.1, -0.2, 0.3], [2.0, 0.5, 1.5]))
+        np.testing.assert_allclose(oc, on[0], rtol=1e-12, atol=1e-14)
+
+
+def test_bf16_rounding():
+    # bfloat16 keeps 8 significant bits: the spacing just above 1 is 2^-7
+    v = np.array([1.0 + 2 ** -8, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, 1.0 + 3 * 2 ** -8, -3.14159])
+    r = M.bf16(v)
+    assert r[0] == 1.0                       # tie -> even (mantissa 0)
+    assert r[1] == 1.0                       # below half
+    assert r[2] == 1.0 + 2 ** -7             # above half
+    assert r[3] == 1.0 + 2 ** -6             # tie -> even (mantissa 2)
+    assert np.all(np.abs(r - v) <= np.abs(v) * 2 ** -8)
+
+
+def test_log_variance_gradient_by_finite_differences():
+    """dL/dtheta from the segment records equals the finite-difference
+    derivative of Var[ln w_theta + lambda N] over the same recorded paths."""
+    wl = W.BM
+    m = wl.model
+    res = T.resolve(m)
+    tab = T.user_table(np.full(16, W.BM_S), np.zeros(16), -0.1, 0.2)
+    p = _params(out_scale=0.2)
+    shift, scale = [0.0, 0.0, 0.0], [20.0, 100.0, 0.2]
+    seg = 64
+    mlp = S.MLPBias(p, segment=seg, in_shift=shift, in_scale=scale, round_bf16=False)
+    trajs = [S.run_segments(m, res, tab, mlp, seed=5, run_id=0, traj=j) for j in range(24)]
+    lam = 0.3
+    loss, g = M.logvar_loss_grad(p, trajs, m.dN, lam, shift, scale, 20.0)
+    # recorded ln w equals the off-policy formula at the sampling parameters
+    for tr in trajs:
+        assert M.logw_at(p, tr, m.dN, shift, scale, 20.0, seg) == pytest.approx(tr["logw"], rel=1e-9, abs=1e-9)
+
+    def L(q):
+        Y = np.array([M.logw_at(q, tr, m.dN, shift, scale, 20.0, seg) + lam * tr["nsteps"] * m.dN
+                      for tr in trajs])
+        return float(np.mean((Y - Y.mean()) ** 2))
+
+    assert L(p) == pytest.approx(loss, rel=1e-9)
+    rng = np.random.default_rng(4)
+    for k in M.KEYS:
+        for _ in range(3):
+            idx = tuple(rng.integers(0, d) for d in p[k].shape)
+            h = 1e-6
+            q = {kk: v.copy() for kk, v in p.items()}
+            q[k][idx] += h
+            fp = L(q)
+            q[k][idx] -= 2 * h
+            fd = (fp - L(q)) / (2 * h)
+            assert abs(fd - g[k][idx]) <= 1e-5 * max(1e-3, abs(fd)) + 1e-9
