@@ -26,7 +26,7 @@
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
  * (seed_lo, seed_hi), counter = (step >> 2, trajectory id, run id, 0); the four
- * 32-bit words become uniforms u_k = ((r_k >> 8) + 0.5) 2^-24 and two
+ * 32-bit words become uniforms u_k = ((r_k >> 9) + 0.5) 2^-23 and two
  * Box-Muller pairs (z0, z1) <- (u0, u1), (z2, z3) <- (u2, u3); step i uses
  * z[i & 3].
  */
@@ -83,7 +83,7 @@ void oracle_normals4(uint64_t seed, uint32_t run_id, uint32_t traj,
     oracle_philox4x32_10(ctr, key, r);
     double u[4];
     for (int k = 0; k < 4; ++k)
-        u[k] = ((double)(r[k] >> 8) + 0.5) * (1.0 / 16777216.0);
+        u[k] = ((double)(r[k] >> 9) + 0.5) * (1.0 / 8388608.0);
     for (int p = 0; p < 2; ++p) {
         double rad = sqrt(-2.0 * log(u[2 * p]));
         double ang = 2.0 * OR_PI * u[2 * p + 1];
