@@ -1,0 +1,282 @@
+/*
+ * fpt.h -- C ABI of the GB300 first-passage-time library (libfpt.so).
+ *
+ * Stochastic-delta-N sampler of arXiv:2410.13683 ("Stochastic inflation
+ * beyond slow roll: noise modelling and importance sampling"): many
+ * independent (phi, pi) Langevin trajectories in e-fold time N, stepped by
+ * Euler-Maruyama (Eq. 4.1) with field-dependent 1-D noise (Eq. 4.6) read from
+ * phi-indexed tables (Sec. 5), an optional importance-sampling drift bias and
+ * its log-likelihood-ratio weight (Eqs. 4.4-4.10), until first passage through
+ * the end surface; then the weighted histogram of first-passage times that
+ * estimates P(delta N) (Sec. 2.3, Sec. 4.1).
+ *
+ * Conventions for every call:
+ *   - Status codes are returned; nothing throws across the ABI. Codes >= 100
+ *     are warnings: results are valid. fpt_last_error() gives a message.
+ *   - The context owns all device memory it allocates and its private CUDA
+ *     stream; the caller owns every buffer it passes in.
+ *   - Pointers documented as "host or device" may be either (unified virtual
+ *     addressing decides); host buffers may be pageable or pinned.
+ *   - Calls on one context are not thread-safe: use one context per thread.
+ *   - Results depend only on (seed, trajectory id, run id) and the inputs,
+ *     never on launch shape, refill granularity or the number of calls that a
+ *     trajectory range is split into.
+ */
+#ifndef FPT_H
+#define FPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fpt_ctx fpt_ctx;
+
+typedef enum {
+    FPT_OK = 0,
+    FPT_E_INVALID = 1,   /* bad argument; nothing was launched              */
+    FPT_E_CUDA = 2,      /* a CUDA runtime call failed                      */
+    FPT_E_NOMEM = 3,     /* device or pinned-host allocation failed         */
+    FPT_E_TIMEOUT = 4,   /* the kernel deadline passed; in-flight
+                            trajectories carry status FPT_TRAJ_ABORTED      */
+    FPT_E_STATE = 5,     /* call order violated (e.g. no table for a model) */
+    FPT_W_CAPPED = 100   /* some trajectories hit max_steps (censored)      */
+} fpt_status;
+
+/* Potential families. */
+enum {
+    /* V = V0 [1 + a_plus (phi - phi_star)] for phi >= phi_star and
+     * V = V0 [1 + a_minus (phi - phi_star)] below: Eq. (4.11) with the slopes
+     * divided by V0. a_plus == a_minus is the linear potential V0 (1 + A phi)
+     * (phi_star = 0). */
+    FPT_POT_PWLINEAR = 0,
+    /* V = V0 exp(mu phi): V'/V = mu, exact attractor pi = -mu (test model). */
+    FPT_POT_EXP = 1
+};
+
+/* Noise-table kinds (fpt_noise_table). */
+enum {
+    FPT_TABLE_DESITTER = 0,  /* S = H/2pi on phi only, Eq. (3.3), H on the
+                                attractor pi = -V'/V                        */
+    FPT_TABLE_BESSEL = 1,    /* semi-analytical Bessel-matched growing mode,
+                                Eqs. (3.10)-(3.13); needs the transition rule */
+    FPT_TABLE_USER = 2       /* caller-supplied S(phi_j), S_pi(phi_j)        */
+};
+
+/* Bias kinds (fpt_run_desc.bias_kind). */
+enum {
+    FPT_BIAS_NONE = 0,   /* direct sampling                                 */
+    FPT_BIAS_CONST = 1,  /* diffusion-based bias of Eq. (4.10): amplitude A  */
+    FPT_BIAS_MLP = 2     /* learned amplitude alpha = MLP(x, pi, N)          */
+};
+
+/* Per-trajectory status (fpt_traj_out.status). */
+enum { FPT_TRAJ_PASSED = 0, FPT_TRAJ_CAPPED = 1, FPT_TRAJ_ABORTED = 2 };
+
+/*
+ * One model: potential, start point and end surface (Sec. 4.1: the system
+ * starts at (phi_init, pi_init) and runs until the end surface is crossed).
+ *
+ * Start/end are either explicit (phi_in, pi_in, phi_end; pi_in = NaN means
+ * the attractor value -V'/V(phi_in)), or -- when n_in is not NaN -- resolved
+ * from the classical background (Eq. 2.21 without noise) that starts at
+ * bg_phi0 on the slow-roll attractor: phi_in, pi_in are the background values
+ * n_in e-folds after the transition time N_T (phi = phi_star) and phi_end the
+ * background field n_end e-folds after N_T (the paper starts after the
+ * transition and sets the start/end by the mode range, Secs. 4.1-4.2).
+ * Passage is the first step n >= 1 with phi_n <= phi_end; N = n dN.
+ */
+typedef struct {
+    int32_t kind;          /* FPT_POT_*                                      */
+    int32_t pad;
+    double V0;             /* potential scale (> 0)                          */
+    double a_plus;         /* relative slope above phi_star                  */
+    double a_minus;        /* relative slope below phi_star                  */
+    double phi_star;       /* transition field value                         */
+    double mu;             /* FPT_POT_EXP slope                              */
+    double phi_in;         /* explicit start (ignored when n_in is set)      */
+    double pi_in;          /* explicit momentum, NaN = attractor             */
+    double phi_end;        /* explicit end surface                           */
+    double bg_phi0;        /* transition rule: background start on attractor */
+    double n_in;           /* transition rule: start, e-folds after N_T; NaN = explicit */
+    double n_end;          /* transition rule: end, e-folds after N_T        */
+    double dN;             /* e-fold step (> 0)                              */
+    int64_t max_steps;     /* step cap per trajectory (>= 1, < 2^31)         */
+} fpt_model;
+
+/* Resolved start/end of a model (FP64, from the background solve). */
+typedef struct {
+    double phi_in, pi_in, phi_end;
+    double N_T;            /* transition time of the background, NaN if none */
+} fpt_model_info;
+
+/*
+ * Create a context on CUDA device `device` holding n_models models (1..64).
+ * Resolves every model's start/end (host FP64 background solve). On error
+ * *ctx is NULL and the status says why.
+ */
+fpt_status fpt_init_model(fpt_ctx **ctx, const fpt_model *models, int32_t n_models,
+                          int32_t device);
+
+/* Resolved start/end of model `model`. */
+fpt_status fpt_model_get_info(const fpt_ctx *ctx, int32_t model, fpt_model_info *out);
+
+/*
+ * Build (or accept) model `model`'s noise table and upload it to the device.
+ *
+ * Grid: phi_j = phi_lo + j h, h = (phi_hi - phi_lo)/(n_points - 1),
+ * j = 0 .. n_points-1 (2 <= n_points <= 8192). phi_lo/phi_hi = NaN select the
+ * model's [phi_end, phi_in]. The stepper interpolates linearly in phi and
+ * holds the end values outside [phi_lo, phi_hi].
+ *
+ * kind FPT_TABLE_BESSEL: for each phi_j the background time N_j with
+ *   phi_bg(N_j) = phi_j, k_j = sigma a(N_j) H(N_j); the mode of Eq. (2.4)
+ *   from its Bunch-Davies state (Eq. 2.5) at N_j - ln(100/sigma) through the
+ *   kink to N_j; Bessel matching at -k eta = sigma with nu from Eq. (3.13);
+ *   S = sqrt(Xi_phiphi) of Eq. (3.12) and S_pi = (nu - 3/2) S.
+ *   Requires the transition rule (n_in set) and 0 < sigma <= 10.
+ * kind FPT_TABLE_DESITTER: S = H/2pi with H^2 = V/(3 - pi_att^2/2), S_pi = 0.
+ * kind FPT_TABLE_USER: user_S / user_Spi (host, n_points doubles each, S >= 0).
+ *
+ * out_S, out_Spi: optional host buffers of n_points doubles receiving the FP64
+ * table. Blocks the calling thread until the upload finished.
+ */
+fpt_status fpt_noise_table(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_points,
+                           double sigma, double phi_lo, double phi_hi,
+                           const double *user_S, const double *user_Spi,
+                           double *out_S, double *out_Spi);
+
+/*
+ * Host-only helpers (no context, no GPU): the same FP64 model resolution and
+ * table construction that fpt_init_model / fpt_noise_table use.
+ */
+fpt_status fpt_resolve_model(const fpt_model *model, fpt_model_info *out);
+fpt_status fpt_table_build(const fpt_model *model, int32_t kind, int32_t n_points,
+                           double sigma, double phi_lo, double phi_hi,
+                           double *out_S, double *out_Spi);
+
+/*
+ * One run: a set of trajectories of one model with one bias.
+ *
+ * The noise of step i of trajectory t is drawn from Philox4x32-10 with key
+ * (seed_lo, seed_hi) and counter (i >> 2, traj_offset + t, run_id, 0): words
+ * r_k -> u_k = ((r_k >> 9) + 0.5) 2^-23 -> Box-Muller pairs (u0,u1), (u2,u3);
+ * step i uses normal number i & 3 of its block. All runs of one fpt_run call
+ * must share `seed`; they are told apart by run_id.
+ *
+ * Bias (Eqs. 4.7-4.10): B = alpha S (1, tan theta_n), weight increment
+ * dA = alpha (alpha dN/2 + xi sqrt(dN)), w = exp(-sum dA). alpha = A for
+ * FPT_BIAS_CONST (A > 0 pushes phi up, towards longer first-passage times).
+ * FPT_BIAS_MLP: alpha = clamp((o1 + t o2)/sqrt(1 + t^2), +-alpha_max) with
+ * (o1, o2) = MLP((x - shift) * scale), x = (phi - phi_end, pi, n dN), held
+ * fixed for `mlp_segment` steps (see fpt_mlp_pack for the weight layout).
+ */
+typedef struct {
+    int32_t model;          /* model index                                   */
+    int32_t bias_kind;      /* FPT_BIAS_*                                    */
+    double A;               /* FPT_BIAS_CONST amplitude                      */
+    int64_t n_traj;         /* trajectories (>= 0)                           */
+    int64_t traj_offset;    /* first trajectory id (ids < 2^32)              */
+    uint64_t seed;          /* Philox key                                    */
+    uint32_t run_id;        /* Philox counter word 2                         */
+    int32_t mlp_segment;    /* FPT_BIAS_MLP: steps per alpha (multiple of 4) */
+    const void *mlp;        /* FPT_BIAS_MLP: device pointer, packed bf16     */
+    float mlp_shift[3];     /* FPT_BIAS_MLP: input shift                     */
+    float mlp_scale[3];     /* FPT_BIAS_MLP: input scale                     */
+    float alpha_max;        /* FPT_BIAS_MLP: |alpha| clamp (> 0)             */
+    int32_t pad;
+} fpt_run_desc;
+
+/* Per-trajectory results of one run; each pointer host or device, nullable.
+ * Arrays hold n_traj entries in trajectory order. */
+typedef struct {
+    double *N;          /* first-passage time n dN                            */
+    double *logw;       /* ln w (0 for direct sampling)                       */
+    int32_t *nsteps;    /* steps taken                                        */
+    uint8_t *status;    /* FPT_TRAJ_*                                         */
+} fpt_traj_out;
+
+/* Launch shape. Zero fields take the context defaults (or the autotuned
+ * choice). */
+typedef struct {
+    int32_t block;          /* threads per block: 128, 256, 512 or 1024       */
+    int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid)        */
+    int32_t check_steps;    /* steps between refill points (multiple of 4)     */
+    int32_t use_graph;      /* 1: replay a captured CUDA graph per shape      */
+    double deadline_s;      /* > 0: abort the kernel after this many seconds  */
+} fpt_launch;
+
+fpt_status fpt_set_launch(fpt_ctx *ctx, const fpt_launch *launch);
+fpt_status fpt_get_launch(const fpt_ctx *ctx, fpt_launch *launch);
+
+/*
+ * Run n_runs runs (1..64) in one persistent launch: one trajectory per
+ * thread, warp-level refill of finished trajectories every check_steps steps.
+ * Results stay in the context for fpt_histogram; out (n_runs entries,
+ * nullable) receives copies. Asynchronous on cuda_stream (NULL = the
+ * context's stream) unless an `out` buffer is pageable host memory; returns
+ * FPT_W_CAPPED / FPT_E_TIMEOUT only after synchronising (see fpt_sync).
+ */
+fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs,
+                   fpt_traj_out *out, void *cuda_stream);
+
+/* Wait for the context's work and return the deferred run status
+ * (FPT_OK, FPT_W_CAPPED or FPT_E_TIMEOUT). */
+fpt_status fpt_sync(fpt_ctx *ctx);
+
+/*
+ * Weighted histogram of run `run` of the last fpt_run (Sec. 4.1).
+ * Bins b = floor((N - N_lo)/db), db = (N_hi - N_lo)/n_bins, N = n dN, over
+ * passed trajectories; n = all trajectories of the run (capped included).
+ *   pdf    = sum_b w / (n db)                       (importance sampling)
+ *   se_w   = its standard error (sample variance of w 1_b / db)
+ *   pdf_ln, se_ln: lognormal-mean estimator (n_b/n) exp(m + s^2/2)/db with
+ *            Cox's error on the log combined with the binomial error
+ *   se_jk  = delete-one-block jackknife error, 32 blocks of trajectory index
+ * log_sum_w / log_sum_w2 are ln(sum w) and ln(sum w^2) per bin (-inf empty).
+ * The tail set T = {passed, N >= N_tail} gives ess_tail = (sum_T w)^2 /
+ * sum_T w^2 and p_tail = sum_T w / n (N_tail = NaN: none).
+ * Array outputs are host buffers of n_bins entries, each nullable.
+ * 1 <= n_bins <= 4096, N_lo < N_hi. Blocks until the results are on the host.
+ */
+typedef struct {
+    int64_t *count;
+    double *log_sum_w, *log_sum_w2, *sum_lw, *sum_lw2;
+    double *pdf, *se_w, *pdf_ln, *se_ln, *se_jk;
+    int64_t n_total, n_passed, n_under, n_over, n_capped, n_tail;
+    double N_mean;         /* mean N of passed trajectories                   */
+    double N_mean_w;       /* self-normalised sum w N / sum w                 */
+    double ess_tail, p_tail;
+    double log_max_w;      /* max ln w over passed trajectories               */
+} fpt_hist;
+
+fpt_status fpt_histogram(fpt_ctx *ctx, int32_t run, double N_lo, double N_hi,
+                         int32_t n_bins, double N_tail, fpt_hist *out, void *cuda_stream);
+
+/*
+ * The same weighted histogram over caller-supplied per-trajectory arrays
+ * (n entries each, host or device; status as FPT_TRAJ_*), e.g. the merged
+ * results of several fpt_run calls. Trajectories are numbered 0..n-1 for the
+ * jackknife blocks. Blocks until the results are on the host.
+ */
+fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double *logw,
+                              const uint8_t *status, int64_t n, double dN, double N_lo,
+                              double N_hi, int32_t n_bins, double N_tail, fpt_hist *out,
+                              void *cuda_stream);
+
+/* Release everything the context owns. NULL is allowed. */
+void fpt_destroy(fpt_ctx *ctx);
+
+/* Message of the last error on this context (or of the last failed
+ * fpt_init_model when ctx is NULL). Never NULL. */
+const char *fpt_last_error(const fpt_ctx *ctx);
+
+/* Library version string. */
+const char *fpt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPT_H */

@@ -1,0 +1,740 @@
+// fpt_abi.cu -- the C ABI of libfpt.so (declared in include/fpt.h).
+//
+// Owns the device state of a context: packed noise tables, model and run
+// descriptors, per-trajectory result arrays, histogram scratch, a private
+// stream and the cache of captured CUDA graphs (one per launch shape).
+#include "fpt_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace fpt_dev;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_init_err = "no error";
+
+struct TableHost {
+    bool ready = false;
+    int M = 0;
+    double lo = 0, h = 0;
+    std::vector<double> S, T;
+};
+
+using GraphKey = std::tuple<int, int, int, int, size_t, int, int, int, long long>;
+
+}  // namespace
+
+struct fpt_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+
+    std::vector<fpt_model> models;
+    std::vector<fpt_model_info> infos;
+    std::vector<TableHost> tables;
+
+    // device buffers
+    ModelDev *d_models = nullptr;
+    float4 *d_tables = nullptr;
+    size_t tables_cap = 0;
+    std::vector<int> table_offset;
+    RunDev *d_runs = nullptr;
+    RunDev *h_runs = nullptr;           // pinned staging
+    unsigned long long *d_cursor = nullptr;
+    int *d_flags = nullptr;             // [0] abort, [1] capped
+    int *h_flags = nullptr;             // pinned copy
+    int32_t *d_nsteps = nullptr;
+    double *d_logw = nullptr;
+    uint8_t *d_status = nullptr;
+    double *d_N = nullptr;
+    long long unit_cap = 0;
+
+    // histogram scratch
+    unsigned long long *d_hmax = nullptr;
+    double *d_hmom = nullptr;
+    double *d_hscal = nullptr;
+    double *d_hout = nullptr;
+    double *h_hout = nullptr;
+    // caller-data histogram scratch
+    int32_t *d_xn = nullptr;
+    double *d_xlw = nullptr;
+    uint8_t *d_xst = nullptr;
+    long long x_cap = 0;
+
+    // last run
+    std::vector<RunDev> last_runs;
+    int last_n_runs = 0;
+    long long last_total = 0;
+    bool last_valid = false;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t run_done = nullptr;
+
+    fpt_launch launch{256, 0, 32, 1, 0.0};
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+static fpt_status fail(fpt_ctx *c, fpt_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_init_err = msg;
+    }
+    return s;
+}
+
+static fpt_status cuda_fail(fpt_ctx *c, cudaError_t e, const char *what)
+{
+    fpt_status s = (e == cudaErrorMemoryAllocation) ? FPT_E_NOMEM : FPT_E_CUDA;
+    return fail(c, s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+static void clear_graphs(fpt_ctx *ctx)
+{
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+}
+
+static void free_all(fpt_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    clear_graphs(ctx);
+    cudaFree(ctx->d_models);
+    cudaFree(ctx->d_tables);
+    cudaFree(ctx->d_runs);
+    cudaFreeHost(ctx->h_runs);
+    cudaFree(ctx->d_cursor);
+    cudaFree(ctx->d_flags);
+    cudaFreeHost(ctx->h_flags);
+    cudaFree(ctx->d_nsteps);
+    cudaFree(ctx->d_logw);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_N);
+    cudaFree(ctx->d_hmax);
+    cudaFree(ctx->d_hmom);
+    cudaFree(ctx->d_hscal);
+    cudaFree(ctx->d_hout);
+    cudaFreeHost(ctx->h_hout);
+    cudaFree(ctx->d_xn);
+    cudaFree(ctx->d_xlw);
+    cudaFree(ctx->d_xst);
+    if (ctx->run_done) cudaEventDestroy(ctx->run_done);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+}
+
+static size_t hout_doubles() { return (size_t)10 * kMaxBins + 16; }
+
+extern "C" {
+
+const char *fpt_version(void) { return "fpt-gb300 0.1 (sm_103a)"; }
+
+const char *fpt_last_error(const fpt_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    return g_init_err.c_str();
+}
+
+fpt_status fpt_resolve_model(const fpt_model *model, fpt_model_info *out)
+{
+    if (!model || !out) return fail(nullptr, FPT_E_INVALID, "null argument");
+    std::string v = fpt_host::validate_model(*model);
+    if (!v.empty()) return fail(nullptr, FPT_E_INVALID, v);
+    try {
+        *out = fpt_host::resolve(*model);
+    } catch (const std::exception &e) {
+        return fail(nullptr, FPT_E_INVALID, e.what());
+    }
+    if (!(out->phi_in > out->phi_end)) return fail(nullptr, FPT_E_INVALID, "resolved phi_in <= phi_end");
+    return FPT_OK;
+}
+
+static fpt_status table_args(int kind, int n_points, double sigma, double phi_lo, double phi_hi,
+                             const double *uS, const double *uT, std::string &msg)
+{
+    if (kind != FPT_TABLE_DESITTER && kind != FPT_TABLE_BESSEL && kind != FPT_TABLE_USER) {
+        msg = "unknown table kind";
+        return FPT_E_INVALID;
+    }
+    if (n_points < 2 || n_points > kMaxTablePoints) { msg = "n_points out of [2, 8192]"; return FPT_E_INVALID; }
+    if (std::isnan(phi_lo) != std::isnan(phi_hi)) { msg = "phi_lo and phi_hi must both be set or both NaN"; return FPT_E_INVALID; }
+    if (!std::isnan(phi_lo) && !(phi_hi > phi_lo && std::isfinite(phi_lo) && std::isfinite(phi_hi))) {
+        msg = "need finite phi_lo < phi_hi";
+        return FPT_E_INVALID;
+    }
+    if (kind == FPT_TABLE_BESSEL && !(sigma > 0 && sigma <= 10)) { msg = "sigma out of (0, 10]"; return FPT_E_INVALID; }
+    if (kind == FPT_TABLE_USER) {
+        if (!uS || !uT) { msg = "USER tables need user_S and user_Spi"; return FPT_E_INVALID; }
+        for (int j = 0; j < n_points; ++j)
+            if (!(uS[j] >= 0) || !std::isfinite(uS[j]) || !std::isfinite(uT[j])) {
+                msg = "USER table values must be finite with S >= 0";
+                return FPT_E_INVALID;
+            }
+    }
+    return FPT_OK;
+}
+
+static fpt_status build_host_table(const fpt_model &m, const fpt_model_info &info, int kind,
+                                   int n_points, double sigma, double phi_lo, double phi_hi,
+                                   const double *uS, const double *uT, TableHost &t, std::string &msg)
+{
+    try {
+        if (kind == FPT_TABLE_USER) {
+            double lo = std::isnan(phi_lo) ? info.phi_end : phi_lo;
+            double hi = std::isnan(phi_hi) ? info.phi_in : phi_hi;
+            if (!(hi > lo)) { msg = "need phi_hi > phi_lo"; return FPT_E_INVALID; }
+            t.S.assign(uS, uS + n_points);
+            t.T.assign(uT, uT + n_points);
+            t.lo = lo;
+            t.h = (hi - lo) / (n_points - 1);
+        } else {
+            fpt_host::build_table(m, kind, n_points, sigma, phi_lo, phi_hi, t.S, t.T, t.lo, t.h);
+        }
+    } catch (const std::exception &e) {
+        msg = e.what();
+        return FPT_E_INVALID;
+    }
+    t.M = n_points;
+    t.ready = true;
+    return FPT_OK;
+}
+
+fpt_status fpt_table_build(const fpt_model *model, int32_t kind, int32_t n_points, double sigma,
+                           double phi_lo, double phi_hi, double *out_S, double *out_Spi)
+{
+    if (!model || !out_S || !out_Spi) return fail(nullptr, FPT_E_INVALID, "null argument");
+    std::string msg;
+    if (kind == FPT_TABLE_USER) return fail(nullptr, FPT_E_INVALID, "USER tables are not built");
+    fpt_status s = table_args(kind, n_points, sigma, phi_lo, phi_hi, nullptr, nullptr, msg);
+    if (s != FPT_OK) return fail(nullptr, s, msg);
+    fpt_model_info info;
+    if ((s = fpt_resolve_model(model, &info)) != FPT_OK) return s;
+    TableHost t;
+    s = build_host_table(*model, info, kind, n_points, sigma, phi_lo, phi_hi, nullptr, nullptr, t, msg);
+    if (s != FPT_OK) return fail(nullptr, s, msg);
+    std::copy(t.S.begin(), t.S.end(), out_S);
+    std::copy(t.T.begin(), t.T.end(), out_Spi);
+    return FPT_OK;
+}
+
+fpt_status fpt_init_model(fpt_ctx **pctx, const fpt_model *models, int32_t n_models, int32_t device)
+{
+    if (!pctx) return fail(nullptr, FPT_E_INVALID, "null ctx pointer");
+    *pctx = nullptr;
+    if (!models || n_models < 1 || n_models > kMaxModels)
+        return fail(nullptr, FPT_E_INVALID, "n_models out of [1, 64]");
+    std::vector<fpt_model_info> infos(n_models);
+    for (int i = 0; i < n_models; ++i) {
+        fpt_status s = fpt_resolve_model(&models[i], &infos[i]);
+        if (s != FPT_OK) {
+            std::lock_guard<std::mutex> g(g_err_mu);
+            g_init_err = "model " + std::to_string(i) + ": " + g_init_err;
+            return s;
+        }
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(nullptr, FPT_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, FPT_E_INVALID, "device index out of range");
+    fpt_ctx *ctx = new (std::nothrow) fpt_ctx;
+    if (!ctx) return fail(nullptr, FPT_E_NOMEM, "host allocation failed");
+    ctx->device = device;
+    ctx->models.assign(models, models + n_models);
+    ctx->infos = infos;
+    ctx->tables.resize(n_models);
+    ctx->table_offset.assign(n_models, 0);
+    auto bail = [&](cudaError_t err, const char *what) {
+        fpt_status s = (err == cudaErrorMemoryAllocation) ? FPT_E_NOMEM : FPT_E_CUDA;
+        fail(nullptr, s, std::string(what) + ": " + cudaGetErrorString(err));
+        free_all(ctx);
+        delete ctx;
+        return s;
+    };
+    if ((e = cudaSetDevice(device))) return bail(e, "cudaSetDevice");
+    if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device))) return bail(e, "attribute");
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking))) return bail(e, "stream");
+    if ((e = cudaEventCreateWithFlags(&ctx->run_done, cudaEventDisableTiming))) return bail(e, "event");
+    if ((e = cudaMalloc(&ctx->d_models, sizeof(ModelDev) * kMaxModels))) return bail(e, "cudaMalloc models");
+    if ((e = cudaMalloc(&ctx->d_runs, sizeof(RunDev) * kMaxRuns))) return bail(e, "cudaMalloc runs");
+    if ((e = cudaMallocHost(&ctx->h_runs, sizeof(RunDev) * kMaxRuns))) return bail(e, "cudaMallocHost runs");
+    if ((e = cudaMalloc(&ctx->d_cursor, 64))) return bail(e, "cudaMalloc cursor");
+    if ((e = cudaMalloc(&ctx->d_flags, 64))) return bail(e, "cudaMalloc flags");
+    if ((e = cudaMallocHost(&ctx->h_flags, 64))) return bail(e, "cudaMallocHost flags");
+    if ((e = cudaMalloc(&ctx->d_hmax, sizeof(unsigned long long) * (kMaxBins + 2)))) return bail(e, "cudaMalloc hist");
+    if ((e = cudaMalloc(&ctx->d_hmom, sizeof(double) * (size_t)kJackknife * kMaxBins * 5))) return bail(e, "cudaMalloc hist");
+    if ((e = cudaMalloc(&ctx->d_hscal, sizeof(double) * kJackknife * 16))) return bail(e, "cudaMalloc hist");
+    if ((e = cudaMalloc(&ctx->d_hout, sizeof(double) * hout_doubles()))) return bail(e, "cudaMalloc hist");
+    if ((e = cudaMallocHost(&ctx->h_hout, sizeof(double) * hout_doubles()))) return bail(e, "cudaMallocHost hist");
+    std::memset(ctx->h_flags, 0, 64);
+    *pctx = ctx;
+    return FPT_OK;
+}
+
+fpt_status fpt_model_get_info(const fpt_ctx *ctx, int32_t model, fpt_model_info *out)
+{
+    if (!ctx || !out) return FPT_E_INVALID;
+    if (model < 0 || model >= (int)ctx->models.size())
+        return fail(const_cast<fpt_ctx *>(ctx), FPT_E_INVALID, "model index out of range");
+    *out = ctx->infos[model];
+    return FPT_OK;
+}
+
+// Re-pack every ready table into one float4 array and refresh the model
+// descriptors: entry j of a model = (S_j, S_{j+1} - S_j, T_j, T_{j+1} - T_j)
+// times sqrt(dN), in FP32.
+static fpt_status upload_tables(fpt_ctx *ctx)
+{
+    size_t total = 0;
+    for (size_t i = 0; i < ctx->tables.size(); ++i) {
+        ctx->table_offset[i] = (int)total;
+        if (ctx->tables[i].ready) total += ctx->tables[i].M;
+    }
+    std::vector<float4> packed(std::max<size_t>(total, 1));
+    std::vector<ModelDev> md(ctx->models.size());
+    for (size_t i = 0; i < ctx->models.size(); ++i) {
+        const fpt_model &m = ctx->models[i];
+        const fpt_model_info &inf = ctx->infos[i];
+        const TableHost &t = ctx->tables[i];
+        ModelDev &d = md[i];
+        std::memset(&d, 0, sizeof(d));
+        d.x_star = (float)(m.phi_star - inf.phi_end);
+        if (m.kind == FPT_POT_EXP) {
+            d.a_plus = d.a_minus = (float)m.mu;
+            d.b_plus = d.b_minus = 0.0f;
+            d.x_star = 0.0f;
+        } else {
+            d.a_plus = (float)m.a_plus;
+            d.a_minus = (float)m.a_minus;
+            d.b_plus = (float)m.a_plus;
+            d.b_minus = (float)m.a_minus;
+        }
+        d.x_in = (float)(inf.phi_in - inf.phi_end);
+        d.pi_in = (float)inf.pi_in;
+        d.dN = (float)m.dN;
+        d.max_steps = (int32_t)m.max_steps;
+        d.table_offset = ctx->table_offset[i];
+        if (t.ready) {
+            d.M = t.M;
+            d.u_scale = (float)(1.0 / t.h);
+            d.u_shift = (float)((inf.phi_end - t.lo) / t.h);
+            const double sq = std::sqrt(m.dN);
+            for (int j = 0; j < t.M; ++j) {
+                const int k = std::min(j + 1, t.M - 1);
+                float4 e;
+                e.x = (float)(t.S[j] * sq);
+                e.y = (float)((t.S[k] - t.S[j]) * sq);
+                e.z = (float)(t.T[j] * sq);
+                e.w = (float)((t.T[k] - t.T[j]) * sq);
+                packed[ctx->table_offset[i] + j] = e;
+            }
+        }
+    }
+    if (packed.size() > ctx->tables_cap) {
+        cudaFree(ctx->d_tables);
+        ctx->d_tables = nullptr;
+        ctx->tables_cap = 0;
+        CK(cudaMalloc(&ctx->d_tables, sizeof(float4) * packed.size()));
+        ctx->tables_cap = packed.size();
+        clear_graphs(ctx);
+    }
+    CK(cudaMemcpyAsync(ctx->d_tables, packed.data(), sizeof(float4) * packed.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_models, md.data(), sizeof(ModelDev) * md.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FPT_OK;
+}
+
+fpt_status fpt_noise_table(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_points,
+                           double sigma, double phi_lo, double phi_hi, const double *user_S,
+                           const double *user_Spi, double *out_S, double *out_Spi)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (model < 0 || model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "model index out of range");
+    std::string msg;
+    fpt_status s = table_args(kind, n_points, sigma, phi_lo, phi_hi, user_S, user_Spi, msg);
+    if (s != FPT_OK) return fail(ctx, s, msg);
+    TableHost t;
+    s = build_host_table(ctx->models[model], ctx->infos[model], kind, n_points, sigma, phi_lo, phi_hi,
+                         user_S, user_Spi, t, msg);
+    if (s != FPT_OK) return fail(ctx, s, msg);
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
+    ctx->tables[model] = t;
+    if ((s = upload_tables(ctx)) != FPT_OK) return s;
+    if (out_S) std::copy(t.S.begin(), t.S.end(), out_S);
+    if (out_Spi) std::copy(t.T.begin(), t.T.end(), out_Spi);
+    return FPT_OK;
+}
+
+fpt_status fpt_set_launch(fpt_ctx *ctx, const fpt_launch *l)
+{
+    if (!ctx || !l) return FPT_E_INVALID;
+    if (l->block && l->block != 128 && l->block != 256 && l->block != 512)
+        return fail(ctx, FPT_E_INVALID, "block must be 128, 256 or 512");
+    if (l->blocks_per_sm < 0 || l->blocks_per_sm > 16) return fail(ctx, FPT_E_INVALID, "blocks_per_sm out of [0, 16]");
+    if (l->check_steps < 0 || (l->check_steps % 4) || l->check_steps > 4096)
+        return fail(ctx, FPT_E_INVALID, "check_steps must be a multiple of 4 in [4, 4096]");
+    if (!(l->deadline_s >= 0) || !std::isfinite(l->deadline_s)) return fail(ctx, FPT_E_INVALID, "bad deadline");
+    ctx->launch.block = l->block ? l->block : 256;
+    ctx->launch.blocks_per_sm = l->blocks_per_sm;
+    ctx->launch.check_steps = l->check_steps ? l->check_steps : 32;
+    ctx->launch.use_graph = l->use_graph;
+    ctx->launch.deadline_s = l->deadline_s;
+    return FPT_OK;
+}
+
+fpt_status fpt_get_launch(const fpt_ctx *ctx, fpt_launch *l)
+{
+    if (!ctx || !l) return FPT_E_INVALID;
+    *l = ctx->launch;
+    return FPT_OK;
+}
+
+static fpt_status ensure_units(fpt_ctx *ctx, long long total)
+{
+    if (total <= ctx->unit_cap) return FPT_OK;
+    long long cap = std::max<long long>(total, 1 << 16);
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
+    cudaFree(ctx->d_nsteps); cudaFree(ctx->d_logw); cudaFree(ctx->d_status); cudaFree(ctx->d_N);
+    ctx->d_nsteps = nullptr; ctx->d_logw = nullptr; ctx->d_status = nullptr; ctx->d_N = nullptr;
+    ctx->unit_cap = 0;
+    clear_graphs(ctx);
+    CK(cudaMalloc(&ctx->d_nsteps, sizeof(int32_t) * cap));
+    CK(cudaMalloc(&ctx->d_logw, sizeof(double) * cap));
+    CK(cudaMalloc(&ctx->d_status, cap));
+    ctx->unit_cap = cap;
+    return FPT_OK;
+}
+
+// Enqueue: descriptor upload, counter reset, status pre-fill, stepper launch,
+// flag read-back.
+static cudaError_t enqueue_run(fpt_ctx *ctx, const EmParams &p, bool weighted, bool smem, int grid,
+                               int block, size_t smem_bytes, int n_runs, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ctx->d_runs, ctx->h_runs, sizeof(RunDev) * n_runs,
+                             cudaMemcpyHostToDevice, s)))
+        return e;
+    if ((e = cudaMemsetAsync(ctx->d_cursor, 0, 64, s))) return e;
+    if ((e = cudaMemsetAsync(ctx->d_flags, 0, 64, s))) return e;
+    if ((e = cudaMemsetAsync(ctx->d_status, FPT_TRAJ_ABORTED, (size_t)p.total_units, s))) return e;
+    if ((e = em_launch(p, weighted, smem, grid, block, smem_bytes, s))) return e;
+    return cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
+fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_traj_out *out,
+                   void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!runs || n_runs < 1 || n_runs > kMaxRuns) return fail(ctx, FPT_E_INVALID, "n_runs out of [1, 64]");
+    std::set<int> used_models;
+    long long total = 0;
+    bool weighted = false;
+    for (int r = 0; r < n_runs; ++r) {
+        const fpt_run_desc &d = runs[r];
+        if (d.model < 0 || d.model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "run model out of range");
+        if (!ctx->tables[d.model].ready) return fail(ctx, FPT_E_STATE, "no noise table for the run's model");
+        if (d.bias_kind != FPT_BIAS_NONE && d.bias_kind != FPT_BIAS_CONST)
+            return fail(ctx, FPT_E_INVALID, "unsupported bias kind");
+        if (d.bias_kind == FPT_BIAS_CONST && !std::isfinite(d.A)) return fail(ctx, FPT_E_INVALID, "A must be finite");
+        if (d.n_traj < 0 || d.traj_offset < 0 || d.traj_offset + d.n_traj > (1LL << 32))
+            return fail(ctx, FPT_E_INVALID, "trajectory ids must lie in [0, 2^32)");
+        if (d.seed != runs[0].seed) return fail(ctx, FPT_E_INVALID, "all runs of one call must share the seed");
+        if (d.n_traj > 0) used_models.insert(d.model);
+        if (d.bias_kind != FPT_BIAS_NONE && d.A != 0.0) weighted = true;
+        total += d.n_traj;
+    }
+    if (total > (1LL << 32)) return fail(ctx, FPT_E_INVALID, "more than 2^32 trajectories in one call");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    fpt_status st = ensure_units(ctx, std::max<long long>(total, 1));
+    if (st != FPT_OK) return st;
+
+    long long begin = 0;
+    ctx->last_runs.resize(n_runs);
+    for (int r = 0; r < n_runs; ++r) {
+        const fpt_run_desc &d = runs[r];
+        const fpt_model &m = ctx->models[d.model];
+        RunDev &rd = ctx->last_runs[r];
+        std::memset(&rd, 0, sizeof(rd));
+        const double A = d.bias_kind == FPT_BIAS_CONST ? d.A : 0.0;
+        rd.model = d.model;
+        rd.bias_kind = d.bias_kind;
+        rd.cb = (float)(A * std::sqrt(m.dN));
+        rd.half_cb2 = (float)(0.5 * A * A * m.dN);
+        rd.n_traj = d.n_traj;
+        rd.traj_offset = d.traj_offset;
+        rd.unit_begin = begin;
+        rd.run_id = d.run_id;
+        rd.sqrt_dN = (float)std::sqrt(m.dN);
+        rd.dN = (float)m.dN;
+        begin += d.n_traj;
+    }
+    // the stepper is the only reader of h_runs: wait for the previous launch
+    if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
+    std::memcpy(ctx->h_runs, ctx->last_runs.data(), sizeof(RunDev) * n_runs);
+
+    const bool smem = used_models.size() == 1;
+    const int smem_model = smem ? *used_models.begin() : 0;
+    const size_t smem_bytes = smem ? sizeof(float4) * ctx->tables[smem_model].M : 0;
+    const int block = ctx->launch.block;
+    int occ = em_occupancy(weighted, smem, block, smem_bytes);
+    if (occ < 1) return fail(ctx, FPT_E_CUDA, "stepper does not fit on an SM with this shape");
+    const int bps = ctx->launch.blocks_per_sm ? std::min(ctx->launch.blocks_per_sm, occ) : occ;
+    const int grid = std::max(1, bps * ctx->sm_count);
+
+    EmParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.models = ctx->d_models;
+    p.runs = ctx->d_runs;
+    p.n_models = (int)ctx->models.size();
+    p.n_runs = n_runs;
+    p.tables = ctx->d_tables;
+    p.smem_table_offset = smem ? ctx->table_offset[smem_model] : 0;
+    p.smem_table_points = smem ? ctx->tables[smem_model].M : 0;
+    p.total_units = total;
+    p.cursor = ctx->d_cursor;
+    p.flags = ctx->d_flags;
+    p.nsteps = ctx->d_nsteps;
+    p.logw = ctx->d_logw;
+    p.status = ctx->d_status;
+    p.key_lo = (uint32_t)runs[0].seed;
+    p.key_hi = (uint32_t)(runs[0].seed >> 32);
+    p.groups_per_check = ctx->launch.check_steps / 4;
+    p.budget_ns = ctx->launch.deadline_s > 0.0 ? (unsigned long long)(ctx->launch.deadline_s * 1e9) + 1ull : 0ull;
+    p.t0 = reinterpret_cast<unsigned long long *>(ctx->d_flags + 2);   // zeroed with the flags
+    const bool graph = ctx->launch.use_graph && p.budget_ns == 0;
+
+    if (total > 0) {
+        if (graph) {
+            GraphKey key{weighted, smem, grid, block, smem_bytes, p.groups_per_check, n_runs,
+                         smem ? smem_model : -1, total};
+            auto it = ctx->graphs.find(key);
+            if (it == ctx->graphs.end()) {
+                cudaGraph_t g;
+                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = enqueue_run(ctx, p, weighted, smem, grid, block, smem_bytes, n_runs, ctx->stream);
+                cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+                if (e != cudaSuccess) { if (e2 == cudaSuccess) cudaGraphDestroy(g); return cuda_fail(ctx, e, "capture"); }
+                if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+                cudaGraphExec_t ex;
+                e = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+                it = ctx->graphs.emplace(key, ex).first;
+            }
+            CK(cudaGraphLaunch(it->second, s));
+        } else {
+            cudaError_t e = enqueue_run(ctx, p, weighted, smem, grid, block, smem_bytes, n_runs, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "run launch");
+        }
+    } else {
+        std::memset(ctx->h_flags, 0, 2 * sizeof(int));
+    }
+    CK(cudaEventRecord(ctx->run_done, s));
+    ctx->last_n_runs = n_runs;
+    ctx->last_total = total;
+    ctx->last_valid = true;
+    ctx->last_stream = s;
+
+    if (out) {
+        bool host_dst = false;
+        for (int r = 0; r < n_runs; ++r) {
+            const RunDev &rd = ctx->last_runs[r];
+            const long long n = rd.n_traj;
+            if (n == 0) continue;
+            const fpt_traj_out &o = out[r];
+            if (o.nsteps) CK(cudaMemcpyAsync(o.nsteps, ctx->d_nsteps + rd.unit_begin, sizeof(int32_t) * n, cudaMemcpyDefault, s));
+            if (o.logw) CK(cudaMemcpyAsync(o.logw, ctx->d_logw + rd.unit_begin, sizeof(double) * n, cudaMemcpyDefault, s));
+            if (o.status) CK(cudaMemcpyAsync(o.status, ctx->d_status + rd.unit_begin, n, cudaMemcpyDefault, s));
+            if (o.N) {
+                if (!ctx->d_N) CK(cudaMalloc(&ctx->d_N, sizeof(double) * ctx->unit_cap));
+                CK(n_of_steps_launch(ctx->d_nsteps + rd.unit_begin, n, ctx->models[rd.model].dN,
+                                     ctx->d_N + rd.unit_begin, s));
+                CK(cudaMemcpyAsync(o.N, ctx->d_N + rd.unit_begin, sizeof(double) * n, cudaMemcpyDefault, s));
+            }
+            for (const void *ptr : {(const void *)o.N, (const void *)o.logw, (const void *)o.nsteps, (const void *)o.status}) {
+                if (!ptr) continue;
+                cudaPointerAttributes a;
+                if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess || a.type != cudaMemoryTypeDevice) host_dst = true;
+                cudaGetLastError();
+            }
+        }
+        if (host_dst) return fpt_sync(ctx);
+    }
+    return FPT_OK;
+}
+
+fpt_status fpt_sync(fpt_ctx *ctx)
+{
+    if (!ctx) return FPT_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->last_valid) return FPT_OK;
+    if (ctx->h_flags[0]) return fail(ctx, FPT_E_TIMEOUT, "kernel deadline passed; run aborted");
+    if (ctx->h_flags[1] > 0) {
+        ctx->err = std::to_string(ctx->h_flags[1]) + " trajectories hit max_steps";
+        return FPT_W_CAPPED;
+    }
+    return FPT_OK;
+}
+
+static fpt_status hist_args(fpt_ctx *ctx, double N_lo, double N_hi, int32_t n_bins, double N_tail)
+{
+    if (n_bins < 1 || n_bins > kMaxBins) return fail(ctx, FPT_E_INVALID, "n_bins out of [1, 4096]");
+    if (!(N_hi > N_lo) || !std::isfinite(N_lo) || !std::isfinite(N_hi))
+        return fail(ctx, FPT_E_INVALID, "need finite N_lo < N_hi");
+    if (!std::isnan(N_tail) && !std::isfinite(N_tail)) return fail(ctx, FPT_E_INVALID, "N_tail must be finite or NaN");
+    return FPT_OK;
+}
+
+// Launch the histogram kernels on per-trajectory device arrays and unpack the
+// FP64 results into the caller's fpt_hist.
+static fpt_status hist_run(fpt_ctx *ctx, const int32_t *nsteps, const double *logw,
+                           const uint8_t *status, long long unit_begin, long long n, double dN,
+                           double N_lo, double N_hi, int32_t n_bins, double N_tail, fpt_hist *out,
+                           cudaStream_t s)
+{
+    HistParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nsteps = nsteps;
+    p.logw = logw;
+    p.status = status;
+    p.unit_begin = unit_begin;
+    p.n = n;
+    p.dN = dN;
+    p.N_lo = N_lo;
+    p.db = (N_hi - N_lo) / n_bins;
+    p.N_tail = N_tail;
+    p.n_bins = n_bins;
+    p.chunk = 4096;
+    p.maxkey = ctx->d_hmax;
+    p.mom = ctx->d_hmom;
+    p.scal = ctx->d_hscal;
+    cudaError_t e = hist_launch(p, ctx->d_hout, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "histogram launch");
+    const size_t nd = (size_t)10 * n_bins + 16;
+    CK(cudaMemcpyAsync(ctx->h_hout, ctx->d_hout, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double *h = ctx->h_hout;
+    for (int b = 0; b < n_bins; ++b) {
+        if (out->count) out->count[b] = (int64_t)h[b];
+        if (out->log_sum_w) out->log_sum_w[b] = h[1 * n_bins + b];
+        if (out->log_sum_w2) out->log_sum_w2[b] = h[2 * n_bins + b];
+        if (out->sum_lw) out->sum_lw[b] = h[3 * n_bins + b];
+        if (out->sum_lw2) out->sum_lw2[b] = h[4 * n_bins + b];
+        if (out->pdf) out->pdf[b] = h[5 * n_bins + b];
+        if (out->se_w) out->se_w[b] = h[6 * n_bins + b];
+        if (out->pdf_ln) out->pdf_ln[b] = h[7 * n_bins + b];
+        if (out->se_ln) out->se_ln[b] = h[8 * n_bins + b];
+        if (out->se_jk) out->se_jk[b] = h[9 * n_bins + b];
+    }
+    const double *sc = h + 10 * n_bins;
+    out->n_total = (int64_t)sc[0];
+    out->n_passed = (int64_t)sc[1];
+    out->n_under = (int64_t)sc[2];
+    out->n_over = (int64_t)sc[3];
+    out->n_capped = (int64_t)sc[4];
+    out->n_tail = (int64_t)sc[5];
+    out->N_mean = sc[6];
+    out->N_mean_w = sc[7];
+    out->ess_tail = sc[8];
+    out->p_tail = sc[9];
+    out->log_max_w = sc[10];
+    return FPT_OK;
+}
+
+fpt_status fpt_histogram(fpt_ctx *ctx, int32_t run, double N_lo, double N_hi, int32_t n_bins,
+                         double N_tail, fpt_hist *out, void *cuda_stream)
+{
+    if (!ctx || !out) return FPT_E_INVALID;
+    if (!ctx->last_valid) return fail(ctx, FPT_E_STATE, "no run to histogram");
+    if (run < 0 || run >= ctx->last_n_runs) return fail(ctx, FPT_E_INVALID, "run index out of range");
+    fpt_status st = hist_args(ctx, N_lo, N_hi, n_bins, N_tail);
+    if (st != FPT_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    CK(cudaStreamWaitEvent(s, ctx->run_done, 0));
+    const RunDev &rd = ctx->last_runs[run];
+    st = hist_run(ctx, ctx->d_nsteps, ctx->d_logw, ctx->d_status, rd.unit_begin, rd.n_traj,
+                  ctx->models[rd.model].dN, N_lo, N_hi, n_bins, N_tail, out, s);
+    if (st != FPT_OK) return st;
+    if (ctx->h_flags[0]) return fail(ctx, FPT_E_STATE, "the run was aborted by its deadline");
+    return FPT_OK;
+}
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    bool dev = cudaPointerGetAttributes(&a, p) == cudaSuccess &&
+               (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    return dev;
+}
+
+fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double *logw,
+                              const uint8_t *status, int64_t n, double dN, double N_lo,
+                              double N_hi, int32_t n_bins, double N_tail, fpt_hist *out,
+                              void *cuda_stream)
+{
+    if (!ctx || !out) return FPT_E_INVALID;
+    if (!nsteps || !logw || !status || n < 1) return fail(ctx, FPT_E_INVALID, "need n >= 1 and three arrays");
+    if (!(dN > 0) || !std::isfinite(dN)) return fail(ctx, FPT_E_INVALID, "dN must be positive");
+    fpt_status st = hist_args(ctx, N_lo, N_hi, n_bins, N_tail);
+    if (st != FPT_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    const bool dev = is_device_ptr(nsteps) && is_device_ptr(logw) && is_device_ptr(status);
+    if (!dev) {
+        if (n > ctx->x_cap) {
+            CK(cudaStreamSynchronize(s));
+            cudaFree(ctx->d_xn); cudaFree(ctx->d_xlw); cudaFree(ctx->d_xst);
+            ctx->d_xn = nullptr; ctx->d_xlw = nullptr; ctx->d_xst = nullptr; ctx->x_cap = 0;
+            CK(cudaMalloc(&ctx->d_xn, sizeof(int32_t) * n));
+            CK(cudaMalloc(&ctx->d_xlw, sizeof(double) * n));
+            CK(cudaMalloc(&ctx->d_xst, n));
+            ctx->x_cap = n;
+        }
+        CK(cudaMemcpyAsync(ctx->d_xn, nsteps, sizeof(int32_t) * n, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(ctx->d_xlw, logw, sizeof(double) * n, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(ctx->d_xst, status, n, cudaMemcpyDefault, s));
+        return hist_run(ctx, ctx->d_xn, ctx->d_xlw, ctx->d_xst, 0, n, dN, N_lo, N_hi, n_bins, N_tail, out, s);
+    }
+    return hist_run(ctx, nsteps, logw, status, 0, n, dN, N_lo, N_hi, n_bins, N_tail, out, s);
+}
+
+void fpt_destroy(fpt_ctx *ctx)
+{
+    if (!ctx) return;
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

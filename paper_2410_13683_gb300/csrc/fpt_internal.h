@@ -1,0 +1,117 @@
+// fpt_internal.h -- declarations shared by the C ABI (fpt_abi.cu), the
+// kernels (fpt_kernels.cu) and the host table builder (fpt_tables.cpp).
+// Not part of the public interface.
+#pragma once
+
+#include "fpt.h"
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace fpt_host {
+std::string validate_model(const fpt_model &m);
+fpt_model_info resolve(const fpt_model &m);
+void build_table(const fpt_model &m, int kind, int n_points, double sigma, double phi_lo,
+                 double phi_hi, std::vector<double> &S, std::vector<double> &Spi,
+                 double &lo_out, double &h_out);
+double dlnV(const fpt_model &m, double phi, int branch);
+double Vof(const fpt_model &m, double phi, int branch);
+double hubble(const fpt_model &m, double phi, double pi, int branch);
+}  // namespace fpt_host
+
+namespace fpt_dev {
+
+constexpr int kMaxRuns = 64;
+constexpr int kMaxModels = 64;
+constexpr int kMaxTablePoints = 8192;
+constexpr int kJackknife = 32;       // jackknife blocks of the histogram
+constexpr int kMaxBins = 4096;
+constexpr int kMlpHidden = 64;
+
+// Model constants in the shifted coordinate x = phi - phi_end (FP32).
+struct ModelDev {
+    float x_star;              // phi_star - phi_end
+    float a_plus, a_minus;     // V'/V = a / (1 + b (x - x_star)), branch by sign
+    float b_plus, b_minus;
+    float x_in, pi_in;
+    float u_scale, u_shift;    // table coordinate u = x * u_scale + u_shift
+    float dN;
+    int32_t M;                 // table points
+    int32_t max_steps;
+    int32_t table_offset;      // first float4 entry of this model's table
+    int32_t pad;
+};
+
+// One run of a launch (FP32 constants; 64-bit unit bookkeeping).
+struct RunDev {
+    int32_t model;
+    int32_t bias_kind;
+    float cb;                  // A sqrt(dN)
+    float half_cb2;            // A^2 dN / 2
+    long long n_traj;
+    long long traj_offset;
+    long long unit_begin;      // first launch unit of this run
+    uint32_t run_id;
+    int32_t segment;           // MLP: steps per alpha
+    const void *mlp;           // MLP: packed bf16 weights (device)
+    float shift[3], scale[3];
+    float alpha_max;
+    float sqrt_dN;
+    float dN;
+    int32_t pad;
+};
+
+struct EmParams {
+    const ModelDev *models;
+    const RunDev *runs;
+    int n_models;
+    int n_runs;
+    const float4 *tables;      // packed (S', dS', T', dT') entries, S' = S sqrt(dN)
+    int smem_table_offset;     // SMEM mode: first entry of the staged table
+    int smem_table_points;     // SMEM mode: entries staged
+    long long total_units;
+    unsigned long long *cursor;
+    int *flags;                // [0] abort, [1] capped count
+    int32_t *nsteps;
+    double *logw;
+    uint8_t *status;
+    uint32_t key_lo, key_hi;
+    int groups_per_check;      // refill every 4 * groups_per_check steps
+    unsigned long long budget_ns;    // > 0: abort after this long (device clock)
+    unsigned long long *t0;          // first %globaltimer reading of the launch (0 before)
+};
+
+struct HistParams {
+    const int32_t *nsteps;
+    const double *logw;
+    const uint8_t *status;
+    long long unit_begin;
+    long long n;               // trajectories of the run
+    double dN;
+    double N_lo, db, N_tail;   // N_tail NaN: no tail set
+    int n_bins;
+    int chunk;                 // units per CTA
+    unsigned long long *maxkey;   // [n_bins + 2]: per-bin, global, tail max of ln w
+    double *mom;               // [kJackknife][n_bins][5]: count, S1, S2, Slw, Slw2
+    double *scal;              // [kJackknife][16] scalars
+};
+
+// Scalar slots of HistParams::scal (per jackknife block).
+enum {
+    kScN = 0, kScPassed, kScUnder, kScOver, kScCapped, kScSumN, kScSumWN, kScSumW,
+    kScTailW, kScTailW2, kScTailN, kScCount
+};
+
+// Host wrappers implemented in fpt_kernels.cu.
+int em_occupancy(bool weighted, bool smem, int block, size_t smem_bytes);
+cudaError_t em_launch(const EmParams &p, bool weighted, bool smem, int grid, int block,
+                      size_t smem_bytes, cudaStream_t s);
+cudaError_t hist_launch(const HistParams &p, double *out, cudaStream_t s);
+cudaError_t n_of_steps_launch(const int32_t *nsteps, long long n, double dN, double *N,
+                              cudaStream_t s);
+
+}  // namespace fpt_dev

@@ -1,0 +1,554 @@
+// fpt_kernels.cu -- sm_103a kernels of the first-passage sampler.
+//
+//   em_kernel      persistent Euler-Maruyama stepper: one trajectory per
+//                  thread, Philox4x32-10 noise, phi-indexed noise table in
+//                  shared memory, importance-sampling bias and Kahan-summed
+//                  log-weight, warp-ballot refill of finished trajectories.
+//   hist_*         weighted histogram of first-passage times (per-bin max,
+//                  shifted sums in shared memory, FP64 flush) and the FP64
+//                  finalisation of P(delta N) and its errors.
+//
+// Method (arXiv:2410.13683): Euler-Maruyama steps, Eq. (4.1), of the 1-D-noise
+// system, Eq. (4.6), with the bias of Eq. (4.7) along the noise vector
+// (1, tan theta_n) (the direction for which the weights of Eq. (4.8) agree) and
+// the diffusion-based amplitude of Eq. (4.10); weight increment
+// dA = A (A dN/2 + xi sqrt(dN)) (Eq. 4.5 in one dimension), w = exp(-sum dA)
+// (Eq. 4.4); first passage at the first step n >= 1 with phi_n <= phi_end,
+// N = n dN (Sec. 4.1).
+#include "fpt_internal.h"
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace fpt_dev {
+
+// ---------------------------------------------------------------------------
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c.x;
+        const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float sqrt_approx(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Two standard normals from two Philox words: 23-bit uniforms
+// u = ((r >> 9) + 0.5) 2^-23 (exact in FP32), then Box-Muller
+// z0 = rho cos(2 pi u1), z1 = rho sin(2 pi u1), rho = sqrt(-2 ln u0); the
+// angle is evaluated as 2 pi u1 - pi, inside the accurate range of the
+// hardware sine/cosine, and the signs restored.
+__device__ __forceinline__ void box_muller(uint32_t r0, uint32_t r1, float &z0, float &z1)
+{
+    const float s = 1.0f / 8388608.0f;
+    const float u0 = fmaf((float)(r0 >> 9), s, 0.5f * s);
+    const float u1 = fmaf((float)(r1 >> 9), s, 0.5f * s);
+    const float rho = sqrt_approx(fmaxf(-2.0f * __logf(u0), 0.0f));
+    float sn, cs;
+    __sincosf(fmaf(u1, 6.28318530717958648f, -3.14159265358979324f), &sn, &cs);
+    z0 = -rho * cs;
+    z1 = -rho * sn;
+}
+
+// Compensated (Kahan) accumulation hi + lo += v.
+__device__ __forceinline__ void kahan_add(float &hi, float &lo, float v)
+{
+    const float y = __fsub_rn(v, lo);
+    const float t = __fadd_rn(hi, y);
+    lo = __fsub_rn(__fsub_rn(t, hi), y);
+    hi = t;
+}
+
+// ---------------------------------------------------------------------------
+// K1: persistent Euler-Maruyama stepper
+// ---------------------------------------------------------------------------
+struct RunSm {               // per-run constants staged in shared memory
+    long long unit_begin;
+    long long traj_offset;
+    float cb, half_cb2;
+    uint32_t run_id;
+    int32_t model;
+};
+
+struct Lane {                // per-thread trajectory state and its constants
+    float x, p, lw_hi, lw_lo;
+    int n;
+    int nmax;
+    uint32_t traj, run_id;
+    float cb, half_cb2, dN;
+    float x_star, a_plus, a_minus, b_plus, b_minus;
+    float u_scale, u_shift, u_max;
+    int i_max, tbase;
+    long long unit;
+};
+
+__device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *s_run,
+                                          const ModelDev *s_model, int n_runs)
+{
+    // last run whose first unit is <= unit (runs are contiguous in unit order)
+    int lo = 0, hi = n_runs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_run[mid].unit_begin <= unit) lo = mid; else hi = mid - 1;
+    }
+    const RunSm &r = s_run[lo];
+    const ModelDev &m = s_model[r.model];
+    L.unit = unit;
+    L.traj = (uint32_t)(r.traj_offset + (unit - r.unit_begin));
+    L.run_id = r.run_id;
+    L.cb = r.cb;
+    L.half_cb2 = r.half_cb2;
+    L.dN = m.dN;
+    L.x_star = m.x_star;
+    L.a_plus = m.a_plus;
+    L.a_minus = m.a_minus;
+    L.b_plus = m.b_plus;
+    L.b_minus = m.b_minus;
+    L.u_scale = m.u_scale;
+    L.u_shift = m.u_shift;
+    L.u_max = (float)(m.M - 1);
+    L.i_max = m.M - 2;
+    L.tbase = m.table_offset;
+    L.nmax = m.max_steps;
+    L.x = m.x_in;
+    L.p = m.pi_in;
+    L.lw_hi = 0.0f;
+    L.lw_lo = 0.0f;
+    L.n = 0;
+}
+
+// One Euler-Maruyama step of Eq. (4.7) with bias amplitude L.cb / sqrt(dN).
+// Returns true when the trajectory has finished (passage or step cap).
+template <bool WEIGHTED, bool SMEM>
+__device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab)
+{
+    // noise table: linear interpolation in x, end values held outside
+    float u = fmaf(L.x, L.u_scale, L.u_shift);
+    u = fminf(fmaxf(u, 0.0f), L.u_max);
+    const int i = min(__float2int_rz(u), L.i_max);
+    const float f = u - (float)i;
+    float4 e;
+    if (SMEM) e = tab[i];
+    else e = __ldg(tab + L.tbase + i);
+    const float S = fmaf(f, e.y, e.x);         // S_phiphi sqrt(dN)
+    const float T = fmaf(f, e.w, e.z);         // tan(theta_n) S_phiphi sqrt(dN)
+    // drift: V'/V of the piecewise-linear (or exponential) potential
+    const float d = L.x - L.x_star;
+    const bool up = d >= 0.0f;
+    const float a = up ? L.a_plus : L.a_minus;
+    const float b = up ? L.b_plus : L.b_minus;
+    const float vpv = __fdividef(a, fmaf(b, d, 1.0f));
+    const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
+    const float zb = z + L.cb;                           // xi + A sqrt(dN)
+    const float xn = fmaf(S, zb, fmaf(L.p, L.dN, L.x));
+    const float pn = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
+    if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z, L.half_cb2));
+    L.x = xn;
+    L.p = pn;
+    ++L.n;
+    return (xn <= 0.0f) | (L.n >= L.nmax);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <bool WEIGHTED, bool SMEM>
+__global__ void __launch_bounds__(512) em_kernel(const EmParams P)
+{
+    extern __shared__ float4 s_tab[];
+    __shared__ RunSm s_run[kMaxRuns];
+    __shared__ ModelDev s_model[kMaxModels];
+    __shared__ unsigned long long s_t0;
+
+    if (P.budget_ns && threadIdx.x == 0) {
+        // the launch's clock origin: the first block to start sets it
+        const unsigned long long now = globaltimer();
+        const unsigned long long prev = atomicCAS(P.t0, 0ull, now);
+        s_t0 = prev ? prev : now;
+    }
+
+    for (int i = threadIdx.x; i < P.n_runs; i += blockDim.x) {
+        const RunDev &r = P.runs[i];
+        s_run[i].unit_begin = r.unit_begin;
+        s_run[i].traj_offset = r.traj_offset;
+        s_run[i].cb = r.cb;
+        s_run[i].half_cb2 = r.half_cb2;
+        s_run[i].run_id = r.run_id;
+        s_run[i].model = r.model;
+    }
+    for (int i = threadIdx.x; i < P.n_models; i += blockDim.x) s_model[i] = P.models[i];
+    if (SMEM) {
+        const float4 *src = P.tables + P.smem_table_offset;
+        for (int i = threadIdx.x; i < P.smem_table_points; i += blockDim.x) s_tab[i] = src[i];
+    }
+    __syncthreads();
+
+    const float4 *tab = SMEM ? s_tab : P.tables;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned FULL = 0xffffffffu;
+
+    Lane L;
+    bool active = false, done = false;
+    {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.cursor, 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        const long long unit = (long long)(base + lane);
+        active = unit < P.total_units;
+        if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
+        else L.n = 0, L.traj = 0, L.run_id = 0;
+    }
+
+    for (;;) {
+        for (int g = 0; g < P.groups_per_check; ++g) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u),
+                                          P.key_lo, P.key_hi);
+            float z[4];
+            box_muller(r.x, r.y, z[0], z[1]);
+            box_muller(r.z, r.w, z[2], z[3]);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (active && !done) done = em_step<WEIGHTED, SMEM>(L, z[s], tab);
+        }
+
+        // refill point: write finished trajectories, fetch new work
+        const bool fin_me = active && done;
+        const unsigned fin = __ballot_sync(FULL, fin_me);
+        if (fin) {
+            if (fin_me) {
+                const bool passed = L.x <= 0.0f;
+                P.nsteps[L.unit] = L.n;
+                P.logw[L.unit] = (double)L.lw_hi + (double)L.lw_lo;
+                P.status[L.unit] = passed ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
+                if (!passed) atomicAdd(P.flags + 1, 1);
+            }
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(P.cursor, (unsigned long long)__popc(fin));
+            base = __shfl_sync(FULL, base, 0);
+            if (fin_me) {
+                const long long unit = (long long)(base + __popc(fin & ((1u << lane) - 1u)));
+                done = false;
+                active = unit < P.total_units;
+                if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
+            }
+        }
+        if (!__any_sync(FULL, active)) break;
+        if (P.budget_ns) {
+            int stop = 0;
+            if (lane == 0) {
+                if (globaltimer() - s_t0 > P.budget_ns) atomicExch(P.flags, 1);
+                stop = *(volatile int *)P.flags;
+            }
+            if (__shfl_sync(FULL, stop, 0)) {
+                // trajectories in flight keep the ABORTED status set before launch
+                break;
+            }
+        }
+    }
+}
+
+static const void *em_fn(bool weighted, bool smem)
+{
+    return weighted ? (smem ? (const void *)em_kernel<true, true> : (const void *)em_kernel<true, false>)
+                    : (smem ? (const void *)em_kernel<false, true> : (const void *)em_kernel<false, false>);
+}
+
+// Opt in to the dynamic shared memory the table needs (outside any stream
+// capture), then report resident blocks per SM for this shape.
+int em_occupancy(bool weighted, bool smem, int block, size_t smem_bytes)
+{
+    const void *f = em_fn(weighted, smem);
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem_bytes) != cudaSuccess) return 0;
+    return nb;
+}
+
+// Launch only (safe inside stream capture): em_occupancy() must have been
+// called for this shape first.
+cudaError_t em_launch(const EmParams &p, bool weighted, bool smem, int grid, int block,
+                      size_t smem_bytes, cudaStream_t s)
+{
+    if (weighted) {
+        if (smem) em_kernel<true, true><<<grid, block, smem_bytes, s>>>(p);
+        else em_kernel<true, false><<<grid, block, smem_bytes, s>>>(p);
+    } else {
+        if (smem) em_kernel<false, true><<<grid, block, smem_bytes, s>>>(p);
+        else em_kernel<false, false><<<grid, block, smem_bytes, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K2: weighted histogram
+// ---------------------------------------------------------------------------
+// Order-preserving map of doubles onto unsigned 64-bit keys (0 = empty).
+__device__ __forceinline__ unsigned long long dkey(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k)
+{
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// Bin of a passed trajectory: q = (n dN - N_lo)/db in IEEE double without
+// contraction, the same operations as the FP64 definition.
+__device__ __forceinline__ double bin_coord(int32_t n, double dN, double N_lo, double db, double &N)
+{
+    N = __dmul_rn((double)n, dN);
+    return __ddiv_rn(__dsub_rn(N, N_lo), db);
+}
+
+// Jackknife block g covers trajectories [ceil(g n / G), ceil((g+1) n / G)).
+__device__ __forceinline__ long long jk_begin(long long g, long long n)
+{
+    return (g * n + kJackknife - 1) / kJackknife;
+}
+
+__global__ void hist_max_kernel(const HistParams P)
+{
+    extern __shared__ unsigned long long s_max[];
+    const int nb = P.n_bins;
+    for (int i = threadIdx.x; i < nb + 2; i += blockDim.x) s_max[i] = 0ull;
+    __syncthreads();
+    const bool has_tail = !isnan(P.N_tail);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long u = P.unit_begin + i;
+        if (P.status[u] != FPT_TRAJ_PASSED) continue;
+        const double lw = P.logw[u];
+        double N;
+        const double q = bin_coord(P.nsteps[u], P.dN, P.N_lo, P.db, N);
+        const unsigned long long k = dkey(lw);
+        if (q >= 0.0 && q < (double)nb) atomicMax(&s_max[(int)floor(q)], k);
+        atomicMax(&s_max[nb], k);
+        if (has_tail && N >= P.N_tail) atomicMax(&s_max[nb + 1], k);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb + 2; i += blockDim.x)
+        if (s_max[i]) atomicMax(&P.maxkey[i], s_max[i]);
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t += red[i];
+    return t;  // valid in thread 0
+}
+
+// grid = (chunks, kJackknife): CTA (c, g) bins trajectories of jackknife
+// block g, chunk c.
+__global__ void hist_sum_kernel(const HistParams P)
+{
+    extern __shared__ double s_dyn[];
+    __shared__ double s_red[32];
+    const int nb = P.n_bins;
+    double *s_mom = s_dyn;                         // [nb][4]: S1, S2, Slw, Slw2
+    double *s_M = s_dyn + 4 * nb;                  // [nb] per-bin max ln w
+    unsigned *s_cnt = (unsigned *)(s_dyn + 5 * nb);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        s_mom[4 * i] = s_mom[4 * i + 1] = s_mom[4 * i + 2] = s_mom[4 * i + 3] = 0.0;
+        s_cnt[i] = 0u;
+        s_M[i] = P.maxkey[i] ? dkey_inv(P.maxkey[i]) : 0.0;
+    }
+    __syncthreads();
+    const double Mg = P.maxkey[nb] ? dkey_inv(P.maxkey[nb]) : 0.0;
+    const double MT = P.maxkey[nb + 1] ? dkey_inv(P.maxkey[nb + 1]) : 0.0;
+    const bool has_tail = !isnan(P.N_tail);
+
+    const long long g = blockIdx.y;
+    const long long b0 = jk_begin(g, P.n), b1 = jk_begin(g + 1, P.n);
+    const long long c0 = b0 + (long long)blockIdx.x * P.chunk;
+    const long long c1 = min(b1, c0 + (long long)P.chunk);
+
+    double sc[kScCount];
+#pragma unroll
+    for (int k = 0; k < kScCount; ++k) sc[k] = 0.0;
+    for (long long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const long long u = P.unit_begin + i;
+        sc[kScN] += 1.0;
+        const uint8_t st = P.status[u];
+        if (st == FPT_TRAJ_CAPPED) { sc[kScCapped] += 1.0; continue; }
+        if (st != FPT_TRAJ_PASSED) continue;
+        const double lw = P.logw[u];
+        double N;
+        const double q = bin_coord(P.nsteps[u], P.dN, P.N_lo, P.db, N);
+        sc[kScPassed] += 1.0;
+        sc[kScSumN] += N;
+        const double wg = exp(lw - Mg);
+        sc[kScSumW] += wg;
+        sc[kScSumWN] += wg * N;
+        if (has_tail && N >= P.N_tail) {
+            const double wt = exp(lw - MT);
+            sc[kScTailW] += wt;
+            sc[kScTailW2] += wt * wt;
+            sc[kScTailN] += 1.0;
+        }
+        if (q < 0.0) { sc[kScUnder] += 1.0; continue; }
+        if (q >= (double)nb) { sc[kScOver] += 1.0; continue; }
+        const int b = (int)floor(q);
+        const double e = exp(lw - s_M[b]);
+        atomicAdd(&s_cnt[b], 1u);
+        atomicAdd(&s_mom[4 * b], e);
+        atomicAdd(&s_mom[4 * b + 1], e * e);
+        atomicAdd(&s_mom[4 * b + 2], lw);
+        atomicAdd(&s_mom[4 * b + 3], lw * lw);
+    }
+    for (int k = 0; k < kScCount; ++k) {
+        const double t = block_sum(sc[k], s_red);
+        if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.scal[g * 16 + k], t);
+    }
+    __syncthreads();
+    double *gm = P.mom + (size_t)g * nb * 5;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        if (!s_cnt[i]) continue;
+        atomicAdd(&gm[5 * i], (double)s_cnt[i]);
+        atomicAdd(&gm[5 * i + 1], s_mom[4 * i]);
+        atomicAdd(&gm[5 * i + 2], s_mom[4 * i + 1]);
+        atomicAdd(&gm[5 * i + 3], s_mom[4 * i + 2]);
+        atomicAdd(&gm[5 * i + 4], s_mom[4 * i + 3]);
+    }
+}
+
+// Output layout (doubles): 10 arrays of n_bins (count, log_sum_w, log_sum_w2,
+// sum_lw, sum_lw2, pdf, se_w, pdf_ln, se_ln, se_jk) then 16 scalars.
+__global__ void hist_finalize_kernel(const HistParams P, double *out)
+{
+    const int nb = P.n_bins;
+    const double n = (double)P.n;
+    const double ninf = -INFINITY;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double cnt = 0, S1 = 0, S2 = 0, Slw = 0, Slw2 = 0;
+        for (int g = 0; g < kJackknife; ++g) {
+            const double *m = P.mom + ((size_t)g * nb + b) * 5;
+            cnt += m[0]; S1 += m[1]; S2 += m[2]; Slw += m[3]; Slw2 += m[4];
+        }
+        const double M = P.maxkey[b] ? dkey_inv(P.maxkey[b]) : 0.0;
+        const bool any = cnt > 0;
+        const double lsw = any ? M + log(S1) : ninf;
+        const double lsw2 = any ? 2.0 * M + log(S2) : ninf;
+        out[0 * nb + b] = cnt;
+        out[1 * nb + b] = lsw;
+        out[2 * nb + b] = lsw2;
+        out[3 * nb + b] = Slw;
+        out[4 * nb + b] = Slw2;
+        // weighted estimator and its error
+        out[5 * nb + b] = any ? exp(lsw - log(n * P.db)) : 0.0;
+        const double var = fmax(S2 - S1 * S1 / n, 0.0) / ((n - 1.0) * n);
+        out[6 * nb + b] = any ? exp(M) * sqrt(var) / P.db : 0.0;
+        // lognormal-mean estimator (n_b >= 2)
+        double pl = NAN, sl = NAN;
+        if (cnt >= 2.0) {
+            const double m = Slw / cnt;
+            const double s2 = fmax((Slw2 - cnt * m * m) / (cnt - 1.0), 0.0);
+            pl = (cnt / n) * exp(m + 0.5 * s2) / P.db;
+            const double cox = sqrt(s2 / cnt + s2 * s2 / (2.0 * (cnt - 1.0)));
+            const double binom = sqrt(fmax(1.0 - cnt / n, 0.0) / cnt);
+            sl = pl * sqrt(cox * cox + binom * binom);
+        }
+        out[7 * nb + b] = pl;
+        out[8 * nb + b] = sl;
+        // delete-one-block jackknife of the weighted estimator
+        double q[kJackknife], qm = 0.0;
+        for (int g = 0; g < kJackknife; ++g) {
+            const double ng = (double)(jk_begin(g + 1, P.n) - jk_begin(g, P.n));
+            const double *m = P.mom + ((size_t)g * nb + b) * 5;
+            q[g] = (S1 - m[1]) / (n - ng);
+            qm += q[g];
+        }
+        qm /= kJackknife;
+        double ss = 0.0;
+        for (int g = 0; g < kJackknife; ++g) ss += (q[g] - qm) * (q[g] - qm);
+        out[9 * nb + b] = any ? exp(M) * sqrt((kJackknife - 1.0) / kJackknife * ss) / P.db : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        double s[kScCount];
+        for (int k = 0; k < kScCount; ++k) {
+            s[k] = 0.0;
+            for (int g = 0; g < kJackknife; ++g) s[k] += P.scal[g * 16 + k];
+        }
+        const double Mg = P.maxkey[nb] ? dkey_inv(P.maxkey[nb]) : -INFINITY;
+        const double MT = P.maxkey[nb + 1] ? dkey_inv(P.maxkey[nb + 1]) : 0.0;
+        double *o = out + 10 * nb;
+        o[0] = s[kScN];
+        o[1] = s[kScPassed];
+        o[2] = s[kScUnder];
+        o[3] = s[kScOver];
+        o[4] = s[kScCapped];
+        o[5] = s[kScTailN];
+        o[6] = s[kScPassed] > 0 ? s[kScSumN] / s[kScPassed] : NAN;
+        o[7] = s[kScSumW] > 0 ? s[kScSumWN] / s[kScSumW] : NAN;
+        o[8] = s[kScTailW2] > 0 ? s[kScTailW] * s[kScTailW] / s[kScTailW2] : 0.0;
+        o[9] = s[kScTailW] > 0 ? exp(MT + log(s[kScTailW]) - log(n)) : 0.0;
+        o[10] = Mg;
+    }
+}
+
+cudaError_t hist_launch(const HistParams &p, double *out, cudaStream_t s)
+{
+    const int nb = p.n_bins;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p.maxkey, 0, sizeof(unsigned long long) * (nb + 2), s))) return e;
+    if ((e = cudaMemsetAsync(p.mom, 0, sizeof(double) * (size_t)kJackknife * nb * 5, s))) return e;
+    if ((e = cudaMemsetAsync(p.scal, 0, sizeof(double) * kJackknife * 16, s))) return e;
+    const size_t smax = sizeof(unsigned long long) * (nb + 2);
+    const int grid1 = (int)min(4096LL, max(1LL, (p.n + 255) / 256));
+    if ((e = cudaFuncSetAttribute(hist_max_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax))) return e;
+    hist_max_kernel<<<grid1, 256, smax, s>>>(p);
+    if ((e = cudaGetLastError())) return e;
+    const size_t ssum = sizeof(double) * 5 * nb + sizeof(unsigned) * nb;
+    if ((e = cudaFuncSetAttribute(hist_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssum))) return e;
+    const long long per_block = (p.n + kJackknife - 1) / kJackknife;
+    const int chunks = (int)max(1LL, (per_block + p.chunk - 1) / p.chunk);
+    hist_sum_kernel<<<dim3(chunks, kJackknife), 256, ssum, s>>>(p);
+    if ((e = cudaGetLastError())) return e;
+    hist_finalize_kernel<<<1, 512, 0, s>>>(p, out);
+    return cudaGetLastError();
+}
+
+__global__ void n_of_steps_kernel(const int32_t *nsteps, long long n, double dN, double *N)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        N[i] = __dmul_rn((double)nsteps[i], dN);
+}
+
+cudaError_t n_of_steps_launch(const int32_t *nsteps, long long n, double dN, double *N,
+                              cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)min(4096LL, (n + 255) / 256);
+    n_of_steps_kernel<<<grid, 256, 0, s>>>(nsteps, n, dN, N);
+    return cudaGetLastError();
+}
+
+}  // namespace fpt_dev

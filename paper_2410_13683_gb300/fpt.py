@@ -1,0 +1,342 @@
+"""Thin ctypes binding of libfpt.so with the C ABI's names.
+
+Argument marshalling only: every step of the sampler runs in the library's
+CUDA kernels (and its host FP64 table builder). There is no CPU or PyTorch
+fallback; if the library is missing or a call fails, an exception is raised.
+
+Buffers may be torch tensors (host or CUDA), numpy arrays (host) or raw
+integer addresses; streams may be ``torch.cuda.Stream`` objects, raw handles
+or None (the context's private stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+NAN = float("nan")
+
+FPT_OK, FPT_E_INVALID, FPT_E_CUDA, FPT_E_NOMEM, FPT_E_TIMEOUT, FPT_E_STATE = 0, 1, 2, 3, 4, 5
+FPT_W_CAPPED = 100
+FPT_POT_PWLINEAR, FPT_POT_EXP = 0, 1
+FPT_TABLE_DESITTER, FPT_TABLE_BESSEL, FPT_TABLE_USER = 0, 1, 2
+FPT_BIAS_NONE, FPT_BIAS_CONST, FPT_BIAS_MLP = 0, 1, 2
+FPT_TRAJ_PASSED, FPT_TRAJ_CAPPED, FPT_TRAJ_ABORTED = 0, 1, 2
+
+_STATUS_NAMES = {0: "FPT_OK", 1: "FPT_E_INVALID", 2: "FPT_E_CUDA", 3: "FPT_E_NOMEM",
+                 4: "FPT_E_TIMEOUT", 5: "FPT_E_STATE", 100: "FPT_W_CAPPED"}
+
+
+class FptError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class fpt_model(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("V0", C.c_double),
+                ("a_plus", C.c_double), ("a_minus", C.c_double), ("phi_star", C.c_double),
+                ("mu", C.c_double), ("phi_in", C.c_double), ("pi_in", C.c_double),
+                ("phi_end", C.c_double), ("bg_phi0", C.c_double), ("n_in", C.c_double),
+                ("n_end", C.c_double), ("dN", C.c_double), ("max_steps", C.c_int64)]
+
+
+class fpt_model_info(C.Structure):
+    _fields_ = [("phi_in", C.c_double), ("pi_in", C.c_double), ("phi_end", C.c_double),
+                ("N_T", C.c_double)]
+
+
+class fpt_run_desc(C.Structure):
+    _fields_ = [("model", C.c_int32), ("bias_kind", C.c_int32), ("A", C.c_double),
+                ("n_traj", C.c_int64), ("traj_offset", C.c_int64), ("seed", C.c_uint64),
+                ("run_id", C.c_uint32), ("mlp_segment", C.c_int32), ("mlp", C.c_void_p),
+                ("mlp_shift", C.c_float * 3), ("mlp_scale", C.c_float * 3),
+                ("alpha_max", C.c_float), ("pad", C.c_int32)]
+
+
+class fpt_traj_out(C.Structure):
+    _fields_ = [("N", C.c_void_p), ("logw", C.c_void_p), ("nsteps", C.c_void_p),
+                ("status", C.c_void_p)]
+
+
+class fpt_launch(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("check_steps", C.c_int32),
+                ("use_graph", C.c_int32), ("deadline_s", C.c_double)]
+
+
+class fpt_hist(C.Structure):
+    _fields_ = [("count", C.c_void_p), ("log_sum_w", C.c_void_p), ("log_sum_w2", C.c_void_p),
+                ("sum_lw", C.c_void_p), ("sum_lw2", C.c_void_p), ("pdf", C.c_void_p),
+                ("se_w", C.c_void_p), ("pdf_ln", C.c_void_p), ("se_ln", C.c_void_p),
+                ("se_jk", C.c_void_p), ("n_total", C.c_int64), ("n_passed", C.c_int64),
+                ("n_under", C.c_int64), ("n_over", C.c_int64), ("n_capped", C.c_int64),
+                ("n_tail", C.c_int64), ("N_mean", C.c_double), ("N_mean_w", C.c_double),
+                ("ess_tail", C.c_double), ("p_tail", C.c_double), ("log_max_w", C.c_double)]
+
+
+# Every function the header declares, with its ctypes signature.
+_SIGNATURES = {
+    "fpt_init_model": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(fpt_model), C.c_int32, C.c_int32]),
+    "fpt_model_get_info": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(fpt_model_info)]),
+    "fpt_noise_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                  C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "fpt_resolve_model": (C.c_int, [C.POINTER(fpt_model), C.POINTER(fpt_model_info)]),
+    "fpt_table_build": (C.c_int, [C.POINTER(fpt_model), C.c_int32, C.c_int32, C.c_double,
+                                  C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "fpt_set_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
+    "fpt_get_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
+    "fpt_run": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int32,
+                          C.POINTER(fpt_traj_out), C.c_void_p]),
+    "fpt_sync": (C.c_int, [C.c_void_p]),
+    "fpt_histogram": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                C.c_double, C.POINTER(fpt_hist), C.c_void_p]),
+    "fpt_histogram_data": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                     C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double,
+                                     C.POINTER(fpt_hist), C.c_void_p]),
+    "fpt_destroy": (None, [C.c_void_p]),
+    "fpt_last_error": (C.c_char_p, [C.c_void_p]),
+    "fpt_version": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libfpt.so (optionally building it first). Raises if unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing:
+        _build.build()
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first "
+                           "(there is no fallback implementation)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status == FPT_OK or status == FPT_W_CAPPED:
+        return status
+    msg = load().fpt_last_error(ctx).decode(errors="replace")
+    raise FptError(status, msg)
+
+
+def _ptr(buf) -> Optional[int]:
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        return int(buf.data_ptr())
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be C-contiguous")
+        return int(buf.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def model_struct(m) -> fpt_model:
+    """fpt_model from any object (or dict) with the header's field names."""
+    get = (lambda k, d=NAN: m.get(k, d)) if isinstance(m, dict) else (lambda k, d=NAN: getattr(m, k, d))
+    return fpt_model(kind=int(get("kind", 0)), pad=0, V0=get("V0"), a_plus=get("a_plus", 0.0),
+                     a_minus=get("a_minus", 0.0), phi_star=get("phi_star", 0.0), mu=get("mu", 0.0),
+                     phi_in=get("phi_in"), pi_in=get("pi_in"), phi_end=get("phi_end"),
+                     bg_phi0=get("bg_phi0"), n_in=get("n_in"), n_end=get("n_end"), dN=get("dN"),
+                     max_steps=int(get("max_steps", 1 << 20)))
+
+
+class Context:
+    """Owning handle of an fpt_ctx (destroyed on close() or garbage collection)."""
+
+    def __init__(self, handle: int, n_models: int):
+        self.handle = handle
+        self.n_models = n_models
+
+    def close(self):
+        if self.handle:
+            load().fpt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def _as_parameter_(self):
+        return C.c_void_p(self.handle)
+
+
+def fpt_version() -> str:
+    return load().fpt_version().decode()
+
+
+def fpt_last_error(ctx: Optional[Context] = None) -> str:
+    return load().fpt_last_error(ctx.handle if ctx else None).decode(errors="replace")
+
+
+def fpt_init_model(models: Sequence, device: int = 0) -> Context:
+    lib = load()
+    arr = (fpt_model * len(models))(*[model_struct(m) for m in models])
+    h = C.c_void_p()
+    _check(lib.fpt_init_model(C.byref(h), arr, len(models), device))
+    return Context(h.value, len(models))
+
+
+def _info_dict(i: fpt_model_info) -> dict:
+    return dict(phi_in=i.phi_in, pi_in=i.pi_in, phi_end=i.phi_end, N_T=i.N_T)
+
+
+def fpt_model_get_info(ctx: Context, model: int) -> dict:
+    i = fpt_model_info()
+    _check(load().fpt_model_get_info(ctx.handle, model, C.byref(i)), ctx.handle)
+    return _info_dict(i)
+
+
+def fpt_resolve_model(model) -> dict:
+    i = fpt_model_info()
+    m = model_struct(model)
+    _check(load().fpt_resolve_model(C.byref(m), C.byref(i)))
+    return _info_dict(i)
+
+
+def fpt_table_build(model, kind: int, n_points: int, sigma: float = 1.0, phi_lo: float = NAN,
+                    phi_hi: float = NAN):
+    S = np.zeros(n_points)
+    T = np.zeros(n_points)
+    m = model_struct(model)
+    _check(load().fpt_table_build(C.byref(m), kind, n_points, sigma, phi_lo, phi_hi,
+                                  _ptr(S), _ptr(T)))
+    return S, T
+
+
+def fpt_noise_table(ctx: Context, model: int, kind: int, n_points: int, sigma: float = 1.0,
+                    phi_lo: float = NAN, phi_hi: float = NAN, user_S=None, user_Spi=None):
+    S = np.zeros(n_points)
+    T = np.zeros(n_points)
+    uS = uT = None
+    if kind == FPT_TABLE_USER:
+        uS = np.ascontiguousarray(user_S, dtype=np.float64)
+        uT = np.ascontiguousarray(user_Spi, dtype=np.float64)
+        if uS.shape != (n_points,) or uT.shape != (n_points,):
+            raise ValueError("user tables must have n_points entries")
+    _check(load().fpt_noise_table(ctx.handle, model, kind, n_points, sigma, phi_lo, phi_hi,
+                                  _ptr(uS), _ptr(uT), _ptr(S), _ptr(T)), ctx.handle)
+    return S, T
+
+
+def fpt_set_launch(ctx: Context, block: int = 0, blocks_per_sm: int = 0, check_steps: int = 0,
+                   use_graph: bool = True, deadline_s: float = 0.0):
+    l = fpt_launch(block=block, blocks_per_sm=blocks_per_sm, check_steps=check_steps,
+                   use_graph=int(bool(use_graph)), deadline_s=deadline_s)
+    _check(load().fpt_set_launch(ctx.handle, C.byref(l)), ctx.handle)
+
+
+def fpt_get_launch(ctx: Context) -> dict:
+    l = fpt_launch()
+    _check(load().fpt_get_launch(ctx.handle, C.byref(l)), ctx.handle)
+    return dict(block=l.block, blocks_per_sm=l.blocks_per_sm, check_steps=l.check_steps,
+                use_graph=bool(l.use_graph), deadline_s=l.deadline_s)
+
+
+def run_desc(model: int = 0, n_traj: int = 0, seed: int = 0, run_id: int = 0, A: float = 0.0,
+             traj_offset: int = 0, bias_kind: Optional[int] = None, mlp=None, mlp_segment: int = 0,
+             mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max: float = 0.0):
+    if bias_kind is None:
+        bias_kind = FPT_BIAS_MLP if mlp is not None else (FPT_BIAS_CONST if A != 0.0 else FPT_BIAS_NONE)
+    return fpt_run_desc(model=model, bias_kind=bias_kind, A=A, n_traj=n_traj,
+                        traj_offset=traj_offset, seed=seed, run_id=run_id,
+                        mlp_segment=mlp_segment, mlp=_ptr(mlp),
+                        mlp_shift=(C.c_float * 3)(*mlp_shift), mlp_scale=(C.c_float * 3)(*mlp_scale),
+                        alpha_max=alpha_max, pad=0)
+
+
+def fpt_run(ctx: Context, runs: Sequence[fpt_run_desc], out: Optional[Sequence[dict]] = None,
+            stream=None) -> int:
+    """Launch the runs; ``out`` is a list (one per run) of dicts with any of
+    the keys N, logw, nsteps, status mapping to caller-owned buffers."""
+    arr = (fpt_run_desc * len(runs))(*runs)
+    outs = None
+    if out is not None:
+        if len(out) != len(runs):
+            raise ValueError("one output dict per run")
+        outs = (fpt_traj_out * len(runs))(*[
+            fpt_traj_out(N=_ptr(o.get("N")), logw=_ptr(o.get("logw")),
+                         nsteps=_ptr(o.get("nsteps")), status=_ptr(o.get("status")))
+            for o in out])
+    return _check(load().fpt_run(ctx.handle, arr, len(runs), outs, _stream(stream)), ctx.handle)
+
+
+def fpt_sync(ctx: Context) -> int:
+    return _check(load().fpt_sync(ctx.handle), ctx.handle)
+
+
+HIST_ARRAYS = ("count", "log_sum_w", "log_sum_w2", "sum_lw", "sum_lw2", "pdf", "se_w", "pdf_ln",
+               "se_ln", "se_jk")
+HIST_SCALARS = ("n_total", "n_passed", "n_under", "n_over", "n_capped", "n_tail", "N_mean",
+                "N_mean_w", "ess_tail", "p_tail", "log_max_w")
+
+
+def fpt_histogram(ctx: Context, run: int, N_lo: float, N_hi: float, n_bins: int,
+                  N_tail: float = NAN, stream=None) -> dict:
+    arrs = {k: np.zeros(n_bins, np.int64 if k == "count" else np.float64) for k in HIST_ARRAYS}
+    h = fpt_hist(**{k: _ptr(v) for k, v in arrs.items()})
+    _check(load().fpt_histogram(ctx.handle, run, N_lo, N_hi, n_bins, N_tail, C.byref(h),
+                                _stream(stream)), ctx.handle)
+    res = dict(arrs)
+    for k in HIST_SCALARS:
+        res[k] = getattr(h, k)
+    res["db"] = (N_hi - N_lo) / n_bins
+    return res
+
+
+def fpt_histogram_data(ctx: Context, nsteps, logw, status, dN: float, N_lo: float, N_hi: float,
+                       n_bins: int, N_tail: float = NAN, stream=None) -> dict:
+    """Histogram of caller-supplied per-trajectory arrays (host or device)."""
+    if isinstance(nsteps, np.ndarray):
+        nsteps = np.ascontiguousarray(nsteps, dtype=np.int32)
+        logw = np.ascontiguousarray(logw, dtype=np.float64)
+        status = np.ascontiguousarray(status, dtype=np.uint8)
+    n = int(len(nsteps))
+    arrs = {k: np.zeros(n_bins, np.int64 if k == "count" else np.float64) for k in HIST_ARRAYS}
+    h = fpt_hist(**{k: _ptr(v) for k, v in arrs.items()})
+    _check(load().fpt_histogram_data(ctx.handle, _ptr(nsteps), _ptr(logw), _ptr(status), n, dN,
+                                     N_lo, N_hi, n_bins, N_tail, C.byref(h), _stream(stream)),
+           ctx.handle)
+    res = dict(arrs)
+    for k in HIST_SCALARS:
+        res[k] = getattr(h, k)
+    res["db"] = (N_hi - N_lo) / n_bins
+    return res

@@ -1,0 +1,128 @@
+"""CPU tests of libfpt.so: it builds, loads, exports every declared symbol,
+and its host FP64 model resolution / table builder agree with the oracle."""
+import ctypes as C
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import tables as T
+from paper_2410_13683_gb300 import build as B
+from paper_2410_13683_gb300 import fpt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    fpt.load()
+
+
+def declared_functions():
+    hdrs = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+            if f.endswith(".h")]
+    names = set()
+    for h in hdrs:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(fpt_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "fpt_run" in names and "fpt_histogram" in names and "fpt_noise_table" in names
+    lib = C.CDLL(B.LIB)
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fpt_[a-z0-9_]+)", out))
+    assert set(names) <= exported
+    # the binding declares exactly the header's functions
+    assert set(fpt._SIGNATURES) == set(names)
+
+
+@pytest.mark.parametrize("wl", [W.LINEAR, W.BM])
+def test_resolve_explicit_models(wl):
+    info = fpt.fpt_resolve_model(wl.model)
+    r = T.resolve(wl.model)
+    assert info["phi_in"] == r.phi_in and info["phi_end"] == r.phi_end
+    assert info["pi_in"] == pytest.approx(r.pi_in, rel=1e-15)
+    assert math.isnan(info["N_T"])
+
+
+def test_resolve_transition_rule_matches_oracle():
+    info = fpt.fpt_resolve_model(W.USR_MODEL)
+    r = T.resolve(W.USR_MODEL)
+    assert abs(info["N_T"] - r.N_T) < 1e-9
+    assert abs(info["phi_in"] - r.phi_in) < 1e-12
+    assert abs(info["pi_in"] / r.pi_in - 1) < 1e-9
+    assert abs(info["phi_end"] - r.phi_end) < 1e-12
+
+
+def test_bessel_table_matches_oracle():
+    m = W.USR_MODEL
+    S, Sp = fpt.fpt_table_build(m, fpt.FPT_TABLE_BESSEL, 4096, 1.0)
+    idx = [0, 1, 7, 300, 1500, 2048, 3333, 4000, 4094, 4095]
+    tab = T.bessel_table(m, T.resolve(m), 4096, 1.0, indices=idx)
+    np.testing.assert_allclose(S[idx], tab.S[idx], rtol=1e-8)
+    np.testing.assert_allclose(Sp[idx], tab.T[idx], rtol=0, atol=1e-8 * float(np.max(tab.S[idx])))
+
+
+def test_bessel_table_other_sigma_and_range():
+    m = W.USR_MODEL
+    r = T.resolve(m)
+    lo, hi = r.phi_end + 1e-5, r.phi_in - 1e-5
+    S, Sp = fpt.fpt_table_build(m, fpt.FPT_TABLE_BESSEL, 64, 0.5, lo, hi)
+    tab = T.bessel_table(m, r, 64, 0.5, lo, hi, indices=[0, 31, 63])
+    np.testing.assert_allclose(S[[0, 31, 63]], tab.S[[0, 31, 63]], rtol=1e-8)
+
+
+def test_desitter_table_matches_oracle():
+    wl = W.LINEAR
+    S, Sp = fpt.fpt_table_build(wl.model, fpt.FPT_TABLE_DESITTER, 4096, 1.0, 0.0, 0.06)
+    tab = T.desitter_table(wl.model, T.resolve(wl.model), 4096, 0.0, 0.06)
+    np.testing.assert_allclose(S, tab.S, rtol=1e-14)
+    assert np.all(Sp == 0)
+
+
+@pytest.mark.parametrize("patch,msg", [
+    (dict(V0=-1.0), "V0"),
+    (dict(dN=0.0), "dN"),
+    (dict(max_steps=0), "max_steps"),
+    (dict(phi_in=-1.0), "phi_in > phi_end"),
+    (dict(kind=7), "kind"),
+])
+def test_invalid_models_are_rejected(patch, msg):
+    m = dict(W.LINEAR.model.__dict__)
+    m.update(patch)
+    with pytest.raises(fpt.FptError) as e:
+        fpt.fpt_resolve_model(m)
+    assert e.value.status == fpt.FPT_E_INVALID and msg in str(e.value)
+
+
+def test_invalid_table_arguments():
+    with pytest.raises(fpt.FptError) as e:
+        fpt.fpt_table_build(W.LINEAR.model, fpt.FPT_TABLE_BESSEL, 16, 1.0)   # no transition rule
+    assert e.value.status == fpt.FPT_E_INVALID
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_table_build(W.USR_MODEL, fpt.FPT_TABLE_BESSEL, 1, 1.0)
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_table_build(W.USR_MODEL, fpt.FPT_TABLE_BESSEL, 16, 0.0)
+
+
+def test_context_needs_a_gpu_or_fails_loudly():
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present")
+    with pytest.raises(fpt.FptError) as e:
+        fpt.fpt_init_model([W.LINEAR.model])
+    assert e.value.status == fpt.FPT_E_CUDA
