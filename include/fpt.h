@@ -211,6 +211,18 @@ fpt_status fpt_set_launch(fpt_ctx *ctx, const fpt_launch *launch);
 fpt_status fpt_get_launch(const fpt_ctx *ctx, fpt_launch *launch);
 
 /*
+ * Autotuner: runs `runs` (each n_traj scaled by `fraction`, 0 < fraction <= 1,
+ * at least 32 trajectories) under every candidate shape -- block in
+ * {128, 256, 512} x check_steps in {8, 32, 128}, resident blocks at maximum
+ * occupancy -- times each with CUDA events after one warm-up, and keeps the
+ * fastest in the context (graph replay and deadline settings are kept).
+ * Results of later runs do not depend on the choice. `chosen` (nullable)
+ * receives it. Synchronous; overwrites the context's last-run results.
+ */
+fpt_status fpt_autotune(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, double fraction,
+                        fpt_launch *chosen);
+
+/*
  * Run n_runs runs (1..64) in one persistent launch: one trajectory per
  * thread, warp-level refill of finished trajectories every check_steps steps.
  * Results stay in the context for fpt_histogram; out (n_runs entries,

@@ -730,6 +730,59 @@ fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double 
     return hist_run(ctx, nsteps, logw, status, 0, n, dN, N_lo, N_hi, n_bins, N_tail, out, s);
 }
 
+fpt_status fpt_autotune(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, double fraction,
+                        fpt_launch *chosen)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!runs || n_runs < 1 || n_runs > kMaxRuns) return fail(ctx, FPT_E_INVALID, "n_runs out of [1, 64]");
+    if (!(fraction > 0.0 && fraction <= 1.0)) return fail(ctx, FPT_E_INVALID, "fraction out of (0, 1]");
+    std::vector<fpt_run_desc> sub(runs, runs + n_runs);
+    for (auto &d : sub)
+        if (d.n_traj > 0) d.n_traj = std::max<int64_t>(32, (int64_t)std::llround(d.n_traj * fraction));
+    const fpt_launch keep = ctx->launch;
+    CK(cudaSetDevice(ctx->device));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    fpt_launch best = keep;
+    float best_ms = -1.0f;
+    fpt_status st = FPT_OK;
+    for (int block : {128, 256, 512}) {
+        for (int check : {8, 32, 128}) {
+            ctx->launch.block = block;
+            ctx->launch.blocks_per_sm = 0;
+            ctx->launch.check_steps = check;
+            ctx->launch.use_graph = keep.use_graph;
+            ctx->launch.deadline_s = 0.0;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && st == FPT_OK; ++rep) {
+                cudaEventRecord(e0, ctx->stream);
+                st = fpt_run(ctx, sub.data(), n_runs, nullptr, nullptr);
+                cudaEventRecord(e1, ctx->stream);
+                if (st == FPT_OK) {
+                    fpt_status s2 = fpt_sync(ctx);
+                    if (s2 != FPT_OK && s2 != FPT_W_CAPPED) st = s2;
+                }
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (st != FPT_OK) break;
+            if (best_ms < 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best = ctx->launch;
+            }
+        }
+        if (st != FPT_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best.use_graph = keep.use_graph;
+    best.deadline_s = keep.deadline_s;
+    ctx->launch = (st == FPT_OK) ? best : keep;
+    if (st != FPT_OK) return st;
+    if (chosen) *chosen = ctx->launch;
+    return FPT_OK;
+}
+
 void fpt_destroy(fpt_ctx *ctx)
 {
     if (!ctx) return;

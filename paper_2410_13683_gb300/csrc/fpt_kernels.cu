@@ -86,7 +86,8 @@ struct RunSm {               // per-run constants staged in shared memory
 };
 
 struct Lane {                // per-thread trajectory state and its constants
-    float x, p, lw_hi, lw_lo;
+    float x, x_c;            // shifted field phi - phi_end as a Kahan pair: x - x_c
+    float p, lw_hi, lw_lo;
     int n;
     int nmax;
     uint32_t traj, run_id;
@@ -126,6 +127,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.tbase = m.table_offset;
     L.nmax = m.max_steps;
     L.x = m.x_in;
+    L.x_c = 0.0f;
     L.p = m.pi_in;
     L.lw_hi = 0.0f;
     L.lw_lo = 0.0f;
@@ -133,7 +135,10 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
 }
 
 // One Euler-Maruyama step of Eq. (4.7) with bias amplitude L.cb / sqrt(dN).
-// Returns true when the trajectory has finished (passage or step cap).
+// The field increment (drift + bias + noise) is formed first and added to the
+// compensated field pair: a plain FP32 field would add the same drift
+// increment to a value on its own grid every step, a rounding error with a
+// fixed sign. Returns true when the trajectory has finished (passage or cap).
 template <bool WEIGHTED, bool SMEM>
 __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab)
 {
@@ -155,13 +160,13 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     const float vpv = __fdividef(a, fmaf(b, d, 1.0f));
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
     const float zb = z + L.cb;                           // xi + A sqrt(dN)
-    const float xn = fmaf(S, zb, fmaf(L.p, L.dN, L.x));
+    const float dx = fmaf(S, zb, L.p * L.dN);           // (pi + alpha S) dN + S xi sqrt(dN)
     const float pn = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
     if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z, L.half_cb2));
-    L.x = xn;
+    kahan_add(L.x, L.x_c, dx);
     L.p = pn;
     ++L.n;
-    return (xn <= 0.0f) | (L.n >= L.nmax);
+    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= L.nmax);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer()
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
         const unsigned fin = __ballot_sync(FULL, fin_me);
         if (fin) {
             if (fin_me) {
-                const bool passed = L.x <= 0.0f;
+                const bool passed = __fsub_rn(L.x, L.x_c) <= 0.0f;
                 P.nsteps[L.unit] = L.n;
                 P.logw[L.unit] = (double)L.lw_hi + (double)L.lw_lo;
                 P.status[L.unit] = passed ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
@@ -441,7 +446,7 @@ __global__ void hist_sum_kernel(const HistParams P)
 
 // Output layout (doubles): 10 arrays of n_bins (count, log_sum_w, log_sum_w2,
 // sum_lw, sum_lw2, pdf, se_w, pdf_ln, se_ln, se_jk) then 16 scalars.
-__global__ void hist_finalize_kernel(const HistParams P, double *out)
+__global__ void __launch_bounds__(128) hist_finalize_kernel(const HistParams P, double *out)
 {
     const int nb = P.n_bins;
     const double n = (double)P.n;
@@ -531,7 +536,7 @@ cudaError_t hist_launch(const HistParams &p, double *out, cudaStream_t s)
     const int chunks = (int)max(1LL, (per_block + p.chunk - 1) / p.chunk);
     hist_sum_kernel<<<dim3(chunks, kJackknife), 256, ssum, s>>>(p);
     if ((e = cudaGetLastError())) return e;
-    hist_finalize_kernel<<<1, 512, 0, s>>>(p, out);
+    hist_finalize_kernel<<<1, 128, 0, s>>>(p, out);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,8 @@ _SIGNATURES = {
                                   C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "fpt_set_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
     "fpt_get_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
+    "fpt_autotune": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int32, C.c_double,
+                               C.POINTER(fpt_launch)]),
     "fpt_run": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int32,
                           C.POINTER(fpt_traj_out), C.c_void_p]),
     "fpt_sync": (C.c_int, [C.c_void_p]),
@@ -267,6 +269,14 @@ def fpt_set_launch(ctx: Context, block: int = 0, blocks_per_sm: int = 0, check_s
 def fpt_get_launch(ctx: Context) -> dict:
     l = fpt_launch()
     _check(load().fpt_get_launch(ctx.handle, C.byref(l)), ctx.handle)
+    return dict(block=l.block, blocks_per_sm=l.blocks_per_sm, check_steps=l.check_steps,
+                use_graph=bool(l.use_graph), deadline_s=l.deadline_s)
+
+
+def fpt_autotune(ctx: Context, runs: Sequence[fpt_run_desc], fraction: float = 0.25) -> dict:
+    arr = (fpt_run_desc * len(runs))(*runs)
+    l = fpt_launch()
+    _check(load().fpt_autotune(ctx.handle, arr, len(runs), fraction, C.byref(l)), ctx.handle)
     return dict(block=l.block, blocks_per_sm=l.blocks_per_sm, check_steps=l.check_steps,
                 use_graph=bool(l.use_graph), deadline_s=l.deadline_s)
 
