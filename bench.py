@@ -189,9 +189,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-traj", type=int, default=1 << 20, help="trajectories per step per GPU")
+    ap.add_argument("--n-traj", type=int, default=1 << 22, help="trajectories per step per GPU")
     ap.add_argument("--ref-traj", type=int, default=1 << 15, help="oracle trajectories per step")
-    ap.add_argument("--cpu-traj", type=int, default=1 << 16, help="CPU-baseline sample size")
+    ap.add_argument("--cpu-traj", type=int, default=1 << 18, help="CPU-baseline sample size")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     args = ap.parse_args()
@@ -218,7 +218,8 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     ctx = fpt.fpt_init_model([m], device=dev)
     S_tab, T_tab = fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     def desc(step):
         return fpt.run_desc(0, n, seed=seed, run_id=step, A=A, traj_offset=rank * n)
@@ -337,7 +338,9 @@ def main():
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "ess_tail_total": ess_total,
+            "em_steps_per_step": steps_tot / args.steps,
             "em_steps_per_s": steps_tot / (sum(run_ms) * 1e-3),
+            "em_launch_ms": mean_run_ms,
             "direct": {"traj_per_s": direct_traj_s, "ess_tail_per_s": direct_ess_s},
             "gain_vs_direct": value / direct_ess_s if direct_ess_s > 0 else None}
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -17,6 +17,9 @@
  *     stream; the caller owns every buffer it passes in.
  *   - Pointers documented as "host or device" may be either (unified virtual
  *     addressing decides); host buffers may be pageable or pinned.
+ *   - `cuda_stream` arguments are cudaStream_t handles; NULL selects the
+ *     context's private stream (cudaStreamLegacy selects the legacy default
+ *     stream).
  *   - Calls on one context are not thread-safe: use one context per thread.
  *   - Results depend only on (seed, trajectory id, run id) and the inputs,
  *     never on launch shape, refill granularity or the number of calls that a
@@ -169,8 +172,11 @@ fpt_status fpt_table_build(const fpt_model *model, int32_t kind, int32_t n_point
  * dA = alpha (alpha dN/2 + xi sqrt(dN)), w = exp(-sum dA). alpha = A for
  * FPT_BIAS_CONST (A > 0 pushes phi up, towards longer first-passage times).
  * FPT_BIAS_MLP: alpha = clamp((o1 + t o2)/sqrt(1 + t^2), +-alpha_max) with
- * (o1, o2) = MLP((x - shift) * scale), x = (phi - phi_end, pi, n dN), held
- * fixed for `mlp_segment` steps (see fpt_mlp_pack for the weight layout).
+ * (o1, o2) = MLP((x - shift) * scale), x = (phi - phi_end, pi, n dN),
+ * t = tan(theta_n) at the segment start, held fixed for `mlp_segment` steps
+ * (steps n = 0, mlp_segment, 2 mlp_segment, ... start a segment). All MLP runs
+ * of one call share blob, segment, shift, scale and alpha_max; a call with MLP
+ * runs refills finished trajectories every mlp_segment steps.
  */
 typedef struct {
     int32_t model;          /* model index                                   */
@@ -276,6 +282,71 @@ fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double 
                               const uint8_t *status, int64_t n, double dN, double N_lo,
                               double N_hi, int32_t n_bins, double N_tail, fpt_hist *out,
                               void *cuda_stream);
+
+/*
+ * ---- Learned importance-sampling proposal (FPT_BIAS_MLP) ----
+ * The paper leaves the optimal bias in the 2-D phase space open (Sec. 5); the
+ * learned proposal replaces the constant amplitude A of Eq. (4.10) by
+ * alpha(x, pi, N) from a 3 -> 64 -> 64 -> 2 SiLU network with bf16 weights
+ * and fp32 accumulation (see fpt_run_desc). Canonical fp32 parameter vector,
+ * FPT_MLP_PARAMS floats, row-major (out, in): W1[64][3], b1[64], W2[64][64],
+ * b2[64], W3[2][64], b3[2].
+ */
+#define FPT_MLP_PARAMS 4546
+#define FPT_MLP_BLOB_BYTES 11808
+
+/* Pack fp32 parameters (host or device, FPT_MLP_PARAMS floats) into the bf16
+ * weight blob the stepper reads (device, FPT_MLP_BLOB_BYTES, 16-byte aligned,
+ * caller-owned). Asynchronous on cuda_stream. */
+fpt_status fpt_mlp_pack(fpt_ctx *ctx, const float *params, void *blob, void *cuda_stream);
+
+/* alpha of the network at normalised inputs s (n x 3) and tan(theta_n) t (n),
+ * with the stepper's own device code; o (n x 2, nullable) receives the raw
+ * outputs. Buffers host or device; blocks until done. */
+fpt_status fpt_mlp_eval(fpt_ctx *ctx, const void *blob, const float *s, const float *tan_t,
+                        int64_t n, float alpha_max, float *alpha, float *o, void *cuda_stream);
+
+/* grad = sum_r dalpha_r d alpha(s_r, t_r) / d theta over n records (the
+ * backward kernel of training, bf16 tensor-core tiles, fp32 accumulation);
+ * zero where |raw alpha| >= alpha_max. params fp32 (host or device); grad
+ * FPT_MLP_PARAMS floats, overwritten. Blocks until done. */
+fpt_status fpt_mlp_grad(fpt_ctx *ctx, const float *params, const float *s, const float *tan_t,
+                        const float *dalpha, int64_t n, float alpha_max, float *grad,
+                        void *cuda_stream);
+
+typedef struct {
+    float lr, beta1, beta2, eps;
+    float clip;            /* > 0: clamp each gradient component first        */
+    int32_t step;          /* Adam step counter (1-based, bias correction)    */
+} fpt_adam;
+
+typedef struct {
+    double loss;           /* Var(Y), Y = ln w + lambda min(N, N_cut)          */
+    double mean_Y;
+    double mean_N;         /* mean first-passage time of the round            */
+    int64_t n_traj;
+    int64_t n_records;     /* segments used for the gradient                  */
+    int64_t n_capped;
+    double grad_norm;      /* L2 norm of the gradient before clipping         */
+} fpt_train_stats;
+
+/*
+ * One training round of the proposal: the run `run` (one FPT_BIAS_MLP run,
+ * run->mlp == blob) is generated in chunks of `chunk` trajectories, recording
+ * every held-alpha segment; then the gradient of the log-variance loss
+ * L = Var[ln w + lambda min(N, N_cut)] at the sampling parameters,
+ *   dL/dtheta = (2/n) sum_j (Y_j - mean_chunk Y) d ln w_j / dtheta,
+ *   d ln w_j / dtheta = -sum_s sqrt(dN) (sum of xi over segment s) d alpha_s / dtheta,
+ * is accumulated, one Adam step updates params / adam_m / adam_v (device,
+ * FPT_MLP_PARAMS floats each) and the blob is re-packed. Returns
+ * FPT_E_NOMEM if a chunk's segment records exceed the record buffer (use a
+ * smaller chunk). Blocks until done; the last chunk stays in the context as
+ * the last run.
+ */
+fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t chunk,
+                               double lambda, double N_cut, const fpt_adam *adam, float *params,
+                               float *adam_m, float *adam_v, void *blob,
+                               fpt_train_stats *stats, void *cuda_stream);
 
 /* Release everything the context owns. NULL is allowed. */
 void fpt_destroy(fpt_ctx *ctx);

@@ -4,6 +4,7 @@
 // descriptors, per-trajectory result arrays, histogram scratch, a private
 // stream and the cache of captured CUDA graphs (one per launch shape).
 #include "fpt_internal.h"
+#include "fpt_mlp.cuh"
 
 #include <cuda_runtime.h>
 
@@ -34,7 +35,7 @@ struct TableHost {
     std::vector<double> S, T;
 };
 
-using GraphKey = std::tuple<int, int, int, int, size_t, int, int, int, long long>;
+using GraphKey = std::tuple<int, int, int, int, size_t, int, int, int, long long, int>;
 
 }  // namespace
 
@@ -86,6 +87,20 @@ struct fpt_ctx {
 
     fpt_launch launch{256, 0, 32, 1, 0.0};
     std::map<GraphKey, cudaGraphExec_t> graphs;
+
+    // learned-proposal training scratch
+    float *d_records = nullptr;
+    long long rec_cap = 0;
+    unsigned long long *d_rec_cursor = nullptr;
+    bool record_mode = false;
+    double *d_Y = nullptr;
+    long long y_cap = 0;
+    float *d_coef = nullptr;
+    long long coef_cap = 0;
+    double *d_acc = nullptr;
+    float *d_grad = nullptr;
+    float *d_tmp = nullptr;
+    long long tmp_cap = 0;
 };
 
 static fpt_status fail(fpt_ctx *c, fpt_status s, const std::string &msg)
@@ -138,6 +153,13 @@ static void free_all(fpt_ctx *ctx)
     cudaFree(ctx->d_hscal);
     cudaFree(ctx->d_hout);
     cudaFreeHost(ctx->h_hout);
+    cudaFree(ctx->d_records);
+    cudaFree(ctx->d_rec_cursor);
+    cudaFree(ctx->d_Y);
+    cudaFree(ctx->d_coef);
+    cudaFree(ctx->d_acc);
+    cudaFree(ctx->d_grad);
+    cudaFree(ctx->d_tmp);
     cudaFree(ctx->d_xn);
     cudaFree(ctx->d_xlw);
     cudaFree(ctx->d_xst);
@@ -146,6 +168,34 @@ static void free_all(fpt_ctx *ctx)
 }
 
 static size_t hout_doubles() { return (size_t)10 * kMaxBins + 16; }
+
+template <class T>
+static fpt_status ensure_dev(fpt_ctx *ctx, T *&ptr, long long &cap, long long need)
+{
+    if (need <= cap) return FPT_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    CK(cudaMalloc(&ptr, sizeof(T) * need));
+    cap = need;
+    return FPT_OK;
+}
+
+__global__ void grad_norm_kernel(const float *g, int n, double *out)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)g[i] * g[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        *out = t;
+    }
+}
 
 extern "C" {
 
@@ -434,7 +484,7 @@ static fpt_status ensure_units(fpt_ctx *ctx, long long total)
 
 // Enqueue: descriptor upload, counter reset, status pre-fill, stepper launch,
 // flag read-back.
-static cudaError_t enqueue_run(fpt_ctx *ctx, const EmParams &p, bool weighted, bool smem, int grid,
+static cudaError_t enqueue_run(fpt_ctx *ctx, const EmParams &p, EmVariant v, int grid,
                                int block, size_t smem_bytes, int n_runs, cudaStream_t s)
 {
     cudaError_t e;
@@ -444,8 +494,9 @@ static cudaError_t enqueue_run(fpt_ctx *ctx, const EmParams &p, bool weighted, b
     if ((e = cudaMemsetAsync(ctx->d_cursor, 0, 64, s))) return e;
     if ((e = cudaMemsetAsync(ctx->d_flags, 0, 64, s))) return e;
     if ((e = cudaMemsetAsync(ctx->d_status, FPT_TRAJ_ABORTED, (size_t)p.total_units, s))) return e;
-    if ((e = em_launch(p, weighted, smem, grid, block, smem_bytes, s))) return e;
-    return cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (v.rec && (e = cudaMemsetAsync(ctx->d_rec_cursor, 0, sizeof(unsigned long long), s))) return e;
+    if ((e = em_launch(p, v, grid, block, smem_bytes, s))) return e;
+    return cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_traj_out *out,
@@ -456,18 +507,36 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     std::set<int> used_models;
     long long total = 0;
     bool weighted = false;
+    int mlp_run = -1;
     for (int r = 0; r < n_runs; ++r) {
         const fpt_run_desc &d = runs[r];
         if (d.model < 0 || d.model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "run model out of range");
         if (!ctx->tables[d.model].ready) return fail(ctx, FPT_E_STATE, "no noise table for the run's model");
-        if (d.bias_kind != FPT_BIAS_NONE && d.bias_kind != FPT_BIAS_CONST)
-            return fail(ctx, FPT_E_INVALID, "unsupported bias kind");
+        if (d.bias_kind != FPT_BIAS_NONE && d.bias_kind != FPT_BIAS_CONST && d.bias_kind != FPT_BIAS_MLP)
+            return fail(ctx, FPT_E_INVALID, "unknown bias kind");
+        if (d.bias_kind == FPT_BIAS_MLP) {
+            if (!d.mlp || (reinterpret_cast<uintptr_t>(d.mlp) & 15))
+                return fail(ctx, FPT_E_INVALID, "MLP runs need a 16-byte aligned device weight blob");
+            if (d.mlp_segment < 4 || d.mlp_segment > 4096 || (d.mlp_segment % 4))
+                return fail(ctx, FPT_E_INVALID, "mlp_segment must be a multiple of 4 in [4, 4096]");
+            if (!(d.alpha_max > 0.0f) || !std::isfinite(d.alpha_max))
+                return fail(ctx, FPT_E_INVALID, "alpha_max must be positive");
+            for (int k = 0; k < 3; ++k)
+                if (!std::isfinite(d.mlp_shift[k]) || !std::isfinite(d.mlp_scale[k]))
+                    return fail(ctx, FPT_E_INVALID, "MLP input shift/scale must be finite");
+            if (mlp_run < 0) mlp_run = r;
+            const fpt_run_desc &q = runs[mlp_run];
+            if (d.mlp != q.mlp || d.mlp_segment != q.mlp_segment || d.alpha_max != q.alpha_max ||
+                std::memcmp(d.mlp_shift, q.mlp_shift, sizeof(q.mlp_shift)) ||
+                std::memcmp(d.mlp_scale, q.mlp_scale, sizeof(q.mlp_scale)))
+                return fail(ctx, FPT_E_INVALID, "all MLP runs of one call must share one proposal");
+        }
         if (d.bias_kind == FPT_BIAS_CONST && !std::isfinite(d.A)) return fail(ctx, FPT_E_INVALID, "A must be finite");
         if (d.n_traj < 0 || d.traj_offset < 0 || d.traj_offset + d.n_traj > (1LL << 32))
             return fail(ctx, FPT_E_INVALID, "trajectory ids must lie in [0, 2^32)");
         if (d.seed != runs[0].seed) return fail(ctx, FPT_E_INVALID, "all runs of one call must share the seed");
         if (d.n_traj > 0) used_models.insert(d.model);
-        if (d.bias_kind != FPT_BIAS_NONE && d.A != 0.0) weighted = true;
+        if ((d.bias_kind == FPT_BIAS_CONST && d.A != 0.0) || d.bias_kind == FPT_BIAS_MLP) weighted = true;
         total += d.n_traj;
     }
     if (total > (1LL << 32)) return fail(ctx, FPT_E_INVALID, "more than 2^32 trajectories in one call");
@@ -494,6 +563,12 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
         rd.run_id = d.run_id;
         rd.sqrt_dN = (float)std::sqrt(m.dN);
         rd.dN = (float)m.dN;
+        if (d.bias_kind == FPT_BIAS_MLP) {
+            rd.segment = d.mlp_segment;
+            rd.mlp = d.mlp;
+            for (int k = 0; k < 3; ++k) { rd.shift[k] = d.mlp_shift[k]; rd.scale[k] = d.mlp_scale[k]; }
+            rd.alpha_max = d.alpha_max;
+        }
         begin += d.n_traj;
     }
     // the stepper is the only reader of h_runs: wait for the previous launch
@@ -502,12 +577,17 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
 
     const bool smem = used_models.size() == 1;
     const int smem_model = smem ? *used_models.begin() : 0;
-    const size_t smem_bytes = smem ? sizeof(float4) * ctx->tables[smem_model].M : 0;
+    const bool mlp = mlp_run >= 0;
+    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode};
+    const size_t smem_bytes = (smem ? sizeof(float4) * ctx->tables[smem_model].M : 0) +
+                              (mlp ? (size_t)kMlpBlobBytes : 0);
     const int block = ctx->launch.block;
-    int occ = em_occupancy(weighted, smem, block, smem_bytes);
+    int occ = em_occupancy(var, block, smem_bytes);
     if (occ < 1) return fail(ctx, FPT_E_CUDA, "stepper does not fit on an SM with this shape");
     const int bps = ctx->launch.blocks_per_sm ? std::min(ctx->launch.blocks_per_sm, occ) : occ;
     const int grid = std::max(1, bps * ctx->sm_count);
+    // the learned proposal is re-evaluated at every refill point
+    const int check_steps = mlp ? runs[mlp_run].mlp_segment : ctx->launch.check_steps;
 
     EmParams p;
     std::memset(&p, 0, sizeof(p));
@@ -526,7 +606,11 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     p.status = ctx->d_status;
     p.key_lo = (uint32_t)runs[0].seed;
     p.key_hi = (uint32_t)(runs[0].seed >> 32);
-    p.groups_per_check = ctx->launch.check_steps / 4;
+    p.groups_per_check = check_steps / 4;
+    p.mlp_run = mlp ? mlp_run : 0;
+    p.records = ctx->d_records;
+    p.rec_cursor = ctx->d_rec_cursor;
+    p.rec_cap = ctx->rec_cap;
     p.budget_ns = ctx->launch.deadline_s > 0.0 ? (unsigned long long)(ctx->launch.deadline_s * 1e9) + 1ull : 0ull;
     p.t0 = reinterpret_cast<unsigned long long *>(ctx->d_flags + 2);   // zeroed with the flags
     const bool graph = ctx->launch.use_graph && p.budget_ns == 0;
@@ -534,12 +618,12 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     if (total > 0) {
         if (graph) {
             GraphKey key{weighted, smem, grid, block, smem_bytes, p.groups_per_check, n_runs,
-                         smem ? smem_model : -1, total};
+                         smem ? smem_model : -1, total, (mlp ? 1 : 0) + (var.rec ? 2 : 0) + 4 * p.mlp_run};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 cudaGraph_t g;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t e = enqueue_run(ctx, p, weighted, smem, grid, block, smem_bytes, n_runs, ctx->stream);
+                cudaError_t e = enqueue_run(ctx, p, var, grid, block, smem_bytes, n_runs, ctx->stream);
                 cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
                 if (e != cudaSuccess) { if (e2 == cudaSuccess) cudaGraphDestroy(g); return cuda_fail(ctx, e, "capture"); }
                 if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
@@ -551,11 +635,11 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             }
             CK(cudaGraphLaunch(it->second, s));
         } else {
-            cudaError_t e = enqueue_run(ctx, p, weighted, smem, grid, block, smem_bytes, n_runs, s);
+            cudaError_t e = enqueue_run(ctx, p, var, grid, block, smem_bytes, n_runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "run launch");
         }
     } else {
-        std::memset(ctx->h_flags, 0, 2 * sizeof(int));
+        std::memset(ctx->h_flags, 0, 4 * sizeof(int));
     }
     CK(cudaEventRecord(ctx->run_done, s));
     ctx->last_n_runs = n_runs;
@@ -715,7 +799,14 @@ fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double 
     if (!dev) {
         if (n > ctx->x_cap) {
             CK(cudaStreamSynchronize(s));
-            cudaFree(ctx->d_xn); cudaFree(ctx->d_xlw); cudaFree(ctx->d_xst);
+            cudaFree(ctx->d_records);
+    cudaFree(ctx->d_rec_cursor);
+    cudaFree(ctx->d_Y);
+    cudaFree(ctx->d_coef);
+    cudaFree(ctx->d_acc);
+    cudaFree(ctx->d_grad);
+    cudaFree(ctx->d_tmp);
+    cudaFree(ctx->d_xn); cudaFree(ctx->d_xlw); cudaFree(ctx->d_xst);
             ctx->d_xn = nullptr; ctx->d_xlw = nullptr; ctx->d_xst = nullptr; ctx->x_cap = 0;
             CK(cudaMalloc(&ctx->d_xn, sizeof(int32_t) * n));
             CK(cudaMalloc(&ctx->d_xlw, sizeof(double) * n));
@@ -780,6 +871,175 @@ fpt_status fpt_autotune(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, 
     ctx->launch = (st == FPT_OK) ? best : keep;
     if (st != FPT_OK) return st;
     if (chosen) *chosen = ctx->launch;
+    return FPT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned proposal
+// ---------------------------------------------------------------------------
+fpt_status fpt_mlp_pack(fpt_ctx *ctx, const float *params, void *blob, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!params || !blob || (reinterpret_cast<uintptr_t>(blob) & 15) || !is_device_ptr(blob))
+        return fail(ctx, FPT_E_INVALID, "need parameters and a 16-byte aligned device blob");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    const float *dp = params;
+    if (!is_device_ptr(params)) {
+        fpt_status st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, kMlpParams);
+        if (st != FPT_OK) return st;
+        CK(cudaMemcpyAsync(ctx->d_tmp, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s));
+        dp = ctx->d_tmp;
+        CK(mlp_pack_launch(dp, blob, s));
+        CK(cudaStreamSynchronize(s));     // the staging buffer is reused
+        return FPT_OK;
+    }
+    CK(mlp_pack_launch(dp, blob, s));
+    return FPT_OK;
+}
+
+fpt_status fpt_mlp_eval(fpt_ctx *ctx, const void *blob, const float *s_in, const float *tan_t, int64_t n,
+                        float alpha_max, float *alpha, float *o, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!blob || !s_in || !tan_t || !alpha || n < 1) return fail(ctx, FPT_E_INVALID, "null buffer or n < 1");
+    if (!(alpha_max > 0.0f)) return fail(ctx, FPT_E_INVALID, "alpha_max must be positive");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    fpt_status st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, 7 * n);
+    if (st != FPT_OK) return st;
+    float *ds = ctx->d_tmp, *dt = ds + 3 * n, *da = dt + n, *dout = da + n;
+    CK(cudaMemcpyAsync(ds, s_in, sizeof(float) * 3 * n, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(dt, tan_t, sizeof(float) * n, cudaMemcpyDefault, s));
+    CK(mlp_eval_launch(blob, ds, dt, n, alpha_max, da, dout, s));
+    CK(cudaMemcpyAsync(alpha, da, sizeof(float) * n, cudaMemcpyDefault, s));
+    if (o) CK(cudaMemcpyAsync(o, dout, sizeof(float) * 2 * n, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return FPT_OK;
+}
+
+fpt_status fpt_mlp_grad(fpt_ctx *ctx, const float *params, const float *s_in, const float *tan_t,
+                        const float *dalpha, int64_t n, float alpha_max, float *grad, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!params || !s_in || !tan_t || !dalpha || !grad || n < 1) return fail(ctx, FPT_E_INVALID, "null buffer or n < 1");
+    if (!(alpha_max > 0.0f)) return fail(ctx, FPT_E_INVALID, "alpha_max must be positive");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    // records (in0, in1, in2, t, -, -, -, -) and the direct dalpha, built on the host
+    std::vector<float> hs(3 * n), ht(n), hd(n), hrec(8 * n, 0.0f), hp(kMlpParams);
+    CK(cudaMemcpy(hs.data(), s_in, sizeof(float) * 3 * n, cudaMemcpyDefault));
+    CK(cudaMemcpy(ht.data(), tan_t, sizeof(float) * n, cudaMemcpyDefault));
+    CK(cudaMemcpy(hd.data(), dalpha, sizeof(float) * n, cudaMemcpyDefault));
+    CK(cudaMemcpy(hp.data(), params, sizeof(float) * kMlpParams, cudaMemcpyDefault));
+    for (int64_t i = 0; i < n; ++i) {
+        hrec[8 * i] = hs[3 * i]; hrec[8 * i + 1] = hs[3 * i + 1]; hrec[8 * i + 2] = hs[3 * i + 2];
+        hrec[8 * i + 3] = ht[i];
+    }
+    fpt_status st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, 9 * n + 2 * kMlpParams);
+    if (st != FPT_OK) return st;
+    float *drec = ctx->d_tmp, *dd = drec + 8 * n, *dp = dd + n, *dg = dp + kMlpParams;
+    CK(cudaMemcpyAsync(drec, hrec.data(), sizeof(float) * 8 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dd, hd.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dp, hp.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dg, 0, sizeof(float) * kMlpParams, s));
+    CK(mlp_bwd_launch(dp, drec, n, nullptr, 0.0f, alpha_max, dd, dg, ctx->sm_count, s));
+    CK(cudaMemcpyAsync(grad, dg, sizeof(float) * kMlpParams, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return FPT_OK;
+}
+
+fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t chunk, double lambda,
+                               double N_cut, const fpt_adam *adam, float *params, float *adam_m,
+                               float *adam_v, void *blob, fpt_train_stats *stats, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!run || !adam || !params || !adam_m || !adam_v || !blob)
+        return fail(ctx, FPT_E_INVALID, "null argument");
+    if (run->bias_kind != FPT_BIAS_MLP || run->mlp != blob)
+        return fail(ctx, FPT_E_INVALID, "the run must use the MLP proposal stored in blob");
+    if (run->n_traj < 2 || chunk < 1) return fail(ctx, FPT_E_INVALID, "need n_traj >= 2 and chunk >= 1");
+    if (!std::isfinite(lambda) || !(N_cut > 0)) return fail(ctx, FPT_E_INVALID, "bad lambda or N_cut");
+    if (!(adam->lr > 0) || adam->step < 1) return fail(ctx, FPT_E_INVALID, "bad Adam settings");
+    if (run->model < 0 || run->model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "run model out of range");
+    if (!is_device_ptr(params) || !is_device_ptr(adam_m) || !is_device_ptr(adam_v))
+        return fail(ctx, FPT_E_INVALID, "params and Adam moments must be device buffers");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    const fpt_model &m = ctx->models[run->model];
+    const long long n_total = run->n_traj;
+    const long long ch = std::min<long long>(chunk, n_total);
+    const long long seg_per_traj = m.max_steps / run->mlp_segment + 2;
+    const long long want = std::min<long long>(ch * seg_per_traj, 1LL << 28);
+    if (want > ctx->rec_cap) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(ctx->d_records);
+        ctx->d_records = nullptr;
+        ctx->rec_cap = 0;
+        clear_graphs(ctx);
+        CK(cudaMalloc(&ctx->d_records, sizeof(float) * 8 * want));
+        ctx->rec_cap = want;
+    }
+    if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
+    if (!ctx->d_acc) CK(cudaMalloc(&ctx->d_acc, 64));
+    if (!ctx->d_grad) CK(cudaMalloc(&ctx->d_grad, sizeof(float) * kMlpParams));
+    fpt_status st = ensure_dev(ctx, ctx->d_coef, ctx->coef_cap, ch);
+    if (st != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_Y, ctx->y_cap, ch)) != FPT_OK) return st;
+    CK(cudaMemsetAsync(ctx->d_grad, 0, sizeof(float) * kMlpParams, s));
+    double sumY = 0, sumY2 = 0, sumN = 0;
+    long long n_rec_total = 0, n_capped = 0, n_passed = 0;
+    for (long long off = 0; off < n_total; off += ch) {
+        fpt_run_desc sub = *run;
+        sub.n_traj = std::min(ch, n_total - off);
+        sub.traj_offset = run->traj_offset + off;
+        ctx->record_mode = true;
+        st = fpt_run(ctx, &sub, 1, nullptr, s);
+        ctx->record_mode = false;
+        if (st != FPT_OK) return st;
+        st = fpt_sync(ctx);
+        if (st == FPT_E_TIMEOUT) return st;
+        if (ctx->h_flags[3]) return fail(ctx, FPT_E_NOMEM, "segment records exceed the record buffer; use a smaller chunk");
+        n_capped += ctx->h_flags[1];
+        unsigned long long n_rec = 0;
+        CK(cudaMemcpy(&n_rec, ctx->d_rec_cursor, sizeof(n_rec), cudaMemcpyDeviceToHost));
+        CK(mlp_coef_launch(ctx->d_nsteps, ctx->d_logw, sub.n_traj, m.dN, lambda, N_cut, 2.0 / (double)n_total,
+                           ctx->d_Y, ctx->d_acc, ctx->d_coef, s));
+        CK(mlp_bwd_launch(params, ctx->d_records, (long long)n_rec, ctx->d_coef, (float)m.dN, run->alpha_max,
+                          nullptr, ctx->d_grad, ctx->sm_count, s));
+        double acc[2];
+        CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+        // mean first-passage time of the chunk
+        fpt_hist h;
+        std::memset(&h, 0, sizeof(h));
+        st = hist_run(ctx, ctx->d_nsteps, ctx->d_logw, ctx->d_status, 0, sub.n_traj, m.dN, 0.0,
+                      (double)m.max_steps * m.dN + 1.0, 1, NAN, &h, s);
+        if (st != FPT_OK) return st;
+        sumY += acc[0];
+        sumY2 += acc[1];
+        sumN += h.N_mean * (double)h.n_passed;
+        n_passed += h.n_passed;
+        n_rec_total += (long long)n_rec;
+    }
+    double gn2 = 0.0;
+    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(double), s));
+    grad_norm_kernel<<<1, 256, 0, s>>>(ctx->d_grad, kMlpParams, ctx->d_acc);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&gn2, ctx->d_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(mlp_adam_launch(params, ctx->d_grad, adam_m, adam_v, kMlpParams, adam->lr, adam->beta1, adam->beta2,
+                       adam->eps, adam->step, adam->clip, s));
+    CK(mlp_pack_launch(params, blob, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        const double mY = sumY / (double)n_total;
+        stats->loss = sumY2 / (double)n_total - mY * mY;
+        stats->mean_Y = mY;
+        stats->mean_N = n_passed ? sumN / (double)n_passed : NAN;
+        stats->n_traj = n_total;
+        stats->n_records = n_rec_total;
+        stats->n_capped = n_capped;
+        stats->grad_norm = std::sqrt(gn2);
+    }
     return FPT_OK;
 }
 

@@ -83,6 +83,12 @@ struct EmParams {
     int groups_per_check;      // refill every 4 * groups_per_check steps
     unsigned long long budget_ns;    // > 0: abort after this long (device clock)
     unsigned long long *t0;          // first %globaltimer reading of the launch (0 before)
+    // learned proposal (MLP variants): launch-wide proposal, from the first MLP run
+    int mlp_run;               // index of a run carrying the proposal parameters
+    // segment records (record variant)
+    float *records;            // [rec_cap][8]
+    unsigned long long *rec_cursor;
+    long long rec_cap;
 };
 
 struct HistParams {
@@ -106,10 +112,28 @@ enum {
     kScTailW, kScTailW2, kScTailN, kScCount
 };
 
+// Stepper variants: weighted (any bias), table in shared memory, learned
+// proposal, segment records.
+struct EmVariant {
+    bool weighted, smem, mlp, rec;
+};
+
 // Host wrappers implemented in fpt_kernels.cu.
-int em_occupancy(bool weighted, bool smem, int block, size_t smem_bytes);
-cudaError_t em_launch(const EmParams &p, bool weighted, bool smem, int grid, int block,
-                      size_t smem_bytes, cudaStream_t s);
+int em_occupancy(EmVariant v, int block, size_t smem_bytes);
+cudaError_t em_launch(const EmParams &p, EmVariant v, int grid, int block, size_t smem_bytes,
+                      cudaStream_t s);
+
+// Host wrappers implemented in fpt_mlp.cu.
+cudaError_t mlp_pack_launch(const float *params, void *blob, cudaStream_t s);
+cudaError_t mlp_eval_launch(const void *blob, const float *s, const float *tan_t, long long n, float amax,
+                            float *alpha, float *o, cudaStream_t st);
+cudaError_t mlp_coef_launch(const int32_t *nsteps, const double *logw, long long n, double dN, double lambda,
+                            double N_cut, double scale, double *Y, double *acc, float *coef, cudaStream_t s);
+cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_rec, const float *coef, float dN,
+                           float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s);
+cudaError_t mlp_adam_launch(float *P, const float *G, float *m, float *v, int n, float lr, float b1, float b2,
+                            float eps, int step, float clip, cudaStream_t s);
+size_t mlp_bwd_smem();
 cudaError_t hist_launch(const HistParams &p, double *out, cudaStream_t s);
 cudaError_t n_of_steps_launch(const int32_t *nsteps, long long n, double dN, double *N,
                               cudaStream_t s);

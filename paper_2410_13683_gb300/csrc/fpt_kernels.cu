@@ -16,6 +16,7 @@
 // (Eq. 4.4); first passage at the first step n >= 1 with phi_n <= phi_end,
 // N = n dN (Sec. 4.1).
 #include "fpt_internal.h"
+#include "fpt_mlp.cuh"
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -83,6 +84,8 @@ struct RunSm {               // per-run constants staged in shared memory
     float cb, half_cb2;
     uint32_t run_id;
     int32_t model;
+    int32_t is_mlp;
+    float sqrt_dN, dN;
 };
 
 struct Lane {                // per-thread trajectory state and its constants
@@ -91,11 +94,18 @@ struct Lane {                // per-thread trajectory state and its constants
     int n;
     int nmax;
     uint32_t traj, run_id;
-    float cb, half_cb2, dN;
+    float cb, half_cb2, dN, sqrt_dN;
     float x_star, a_plus, a_minus, b_plus, b_minus;
     float u_scale, u_shift, u_max;
     int i_max, tbase;
+    bool mlp;
     long long unit;
+};
+
+struct SegRec {              // open segment of the record variant
+    float in0, in1, in2, tan_t, raw, sum_xi;
+    int n0;
+    bool open;
 };
 
 __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *s_run,
@@ -114,7 +124,9 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.run_id = r.run_id;
     L.cb = r.cb;
     L.half_cb2 = r.half_cb2;
+    L.mlp = r.is_mlp != 0;
     L.dN = m.dN;
+    L.sqrt_dN = r.sqrt_dN;
     L.x_star = m.x_star;
     L.a_plus = m.a_plus;
     L.a_minus = m.a_minus;
@@ -134,6 +146,17 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.n = 0;
 }
 
+// Table entry (S', dS', T', dT') and interpolation weight at the lane's field.
+template <bool SMEM>
+__device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restrict__ tab, float &f)
+{
+    float u = fmaf(L.x, L.u_scale, L.u_shift);
+    u = fminf(fmaxf(u, 0.0f), L.u_max);
+    const int i = min(__float2int_rz(u), L.i_max);
+    f = u - (float)i;
+    return SMEM ? tab[i] : __ldg(tab + L.tbase + i);
+}
+
 // One Euler-Maruyama step of Eq. (4.7) with bias amplitude L.cb / sqrt(dN).
 // The field increment (drift + bias + noise) is formed first and added to the
 // compensated field pair: a plain FP32 field would add the same drift
@@ -143,13 +166,8 @@ template <bool WEIGHTED, bool SMEM>
 __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab)
 {
     // noise table: linear interpolation in x, end values held outside
-    float u = fmaf(L.x, L.u_scale, L.u_shift);
-    u = fminf(fmaxf(u, 0.0f), L.u_max);
-    const int i = min(__float2int_rz(u), L.i_max);
-    const float f = u - (float)i;
-    float4 e;
-    if (SMEM) e = tab[i];
-    else e = __ldg(tab + L.tbase + i);
+    float f;
+    const float4 e = table_at<SMEM>(L, tab, f);
     const float S = fmaf(f, e.y, e.x);         // S_phiphi sqrt(dN)
     const float T = fmaf(f, e.w, e.z);         // tan(theta_n) S_phiphi sqrt(dN)
     // drift: V'/V of the piecewise-linear (or exponential) potential
@@ -159,7 +177,7 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     const float b = up ? L.b_plus : L.b_minus;
     const float vpv = __fdividef(a, fmaf(b, d, 1.0f));
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
-    const float zb = z + L.cb;                           // xi + A sqrt(dN)
+    const float zb = z + L.cb;                           // xi + alpha sqrt(dN)
     const float dx = fmaf(S, zb, L.p * L.dN);           // (pi + alpha S) dN + S xi sqrt(dN)
     const float pn = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
     if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z, L.half_cb2));
@@ -176,10 +194,42 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-template <bool WEIGHTED, bool SMEM>
+// Learned proposal at a segment start: alpha from the warp's MLP evaluation
+// at the current state; every lane of the warp takes part.
+template <bool SMEM, bool REC>
+__device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg, const float4 *tab,
+                                                  const uint2 *tiles, const float *bias, const RunDev &pr)
+{
+    float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f, tan_t = 0.0f;
+    if (live) {
+        in0 = (__fsub_rn(L.x, L.x_c) - pr.shift[0]) * pr.scale[0];
+        in1 = (L.p - pr.shift[1]) * pr.scale[1];
+        in2 = ((float)L.n * L.dN - pr.shift[2]) * pr.scale[2];
+        float f;
+        const float4 e = table_at<SMEM>(L, tab, f);
+        const float S = fmaf(f, e.y, e.x), T = fmaf(f, e.w, e.z);
+        tan_t = S > 0.0f ? __fdividef(T, S) : 0.0f;
+    }
+    float o1, o2;
+    mlp_forward_warp(tiles, bias, in0, in1, in2, o1, o2);
+    if (live) {
+        float raw;
+        const float al = mlp_alpha_of(o1, o2, tan_t, pr.alpha_max, raw);
+        L.cb = al * L.sqrt_dN;
+        L.half_cb2 = 0.5f * al * al * L.dN;
+        if (REC) {
+            sg.in0 = in0; sg.in1 = in1; sg.in2 = in2; sg.tan_t = tan_t; sg.raw = raw;
+            sg.sum_xi = 0.0f;
+            sg.n0 = L.n;
+            sg.open = true;
+        }
+    }
+}
+
+template <bool WEIGHTED, bool SMEM, bool MLP, bool REC>
 __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
 {
-    extern __shared__ float4 s_tab[];
+    extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
     __shared__ ModelDev s_model[kMaxModels];
     __shared__ unsigned long long s_t0;
@@ -190,7 +240,6 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
         const unsigned long long prev = atomicCAS(P.t0, 0ull, now);
         s_t0 = prev ? prev : now;
     }
-
     for (int i = threadIdx.x; i < P.n_runs; i += blockDim.x) {
         const RunDev &r = P.runs[i];
         s_run[i].unit_begin = r.unit_begin;
@@ -199,11 +248,23 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
         s_run[i].half_cb2 = r.half_cb2;
         s_run[i].run_id = r.run_id;
         s_run[i].model = r.model;
+        s_run[i].is_mlp = r.bias_kind == FPT_BIAS_MLP;
+        s_run[i].sqrt_dN = r.sqrt_dN;
+        s_run[i].dN = r.dN;
     }
     for (int i = threadIdx.x; i < P.n_models; i += blockDim.x) s_model[i] = P.models[i];
     if (SMEM) {
         const float4 *src = P.tables + P.smem_table_offset;
         for (int i = threadIdx.x; i < P.smem_table_points; i += blockDim.x) s_tab[i] = src[i];
+    }
+    // MLP variants: the proposal's fragment blob follows the table in shared memory
+    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + (SMEM ? P.smem_table_points : 0));
+    float *s_bias = reinterpret_cast<float *>(s_tiles + kMlpTiles * 32);
+    const RunDev &prun = P.runs[MLP ? P.mlp_run : 0];
+    if (MLP) {
+        const float4 *src = reinterpret_cast<const float4 *>(prun.mlp);
+        float4 *dst = reinterpret_cast<float4 *>(s_tiles);
+        for (int i = threadIdx.x; i < kMlpBlobBytes / 16; i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
 
@@ -212,6 +273,8 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
     const unsigned FULL = 0xffffffffu;
 
     Lane L;
+    SegRec sg;
+    sg.open = false;
     bool active = false, done = false;
     {
         unsigned long long base = 0;
@@ -220,10 +283,13 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
         const long long unit = (long long)(base + lane);
         active = unit < P.total_units;
         if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
-        else L.n = 0, L.traj = 0, L.run_id = 0;
+        else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false;
     }
 
     for (;;) {
+        if (MLP && __any_sync(FULL, active && L.mlp))
+            mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun);
+
         for (int g = 0; g < P.groups_per_check; ++g) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u),
                                           P.key_lo, P.key_hi);
@@ -232,7 +298,33 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
             box_muller(r.z, r.w, z[2], z[3]);
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                if (active && !done) done = em_step<WEIGHTED, SMEM>(L, z[s], tab);
+                if (active && !done) {
+                    if (REC) sg.sum_xi += z[s];
+                    done = em_step<WEIGHTED, SMEM>(L, z[s], tab);
+                }
+        }
+
+        if (REC) {
+            // close the segments of this interval: (inputs, tan, raw alpha, sum xi, unit, steps)
+            const bool wr = active && sg.open;
+            const unsigned m = __ballot_sync(FULL, wr);
+            if (m) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(P.rec_cursor, (unsigned long long)__popc(m));
+                base = __shfl_sync(FULL, base, 0);
+                if (wr) {
+                    const long long idx = (long long)(base + __popc(m & ((1u << lane) - 1u)));
+                    if (idx < P.rec_cap) {
+                        float4 *q = reinterpret_cast<float4 *>(P.records + 8 * idx);
+                        q[0] = make_float4(sg.in0, sg.in1, sg.in2, sg.tan_t);
+                        q[1] = make_float4(sg.raw, sg.sum_xi, __uint_as_float((uint32_t)L.unit),
+                                           __int_as_float(L.n - sg.n0));
+                    } else {
+                        atomicExch(P.flags + 3, 1);
+                    }
+                }
+            }
+            sg.open = false;
         }
 
         // refill point: write finished trajectories, fetch new work
@@ -271,17 +363,19 @@ __global__ void __launch_bounds__(512) em_kernel(const EmParams P)
     }
 }
 
-static const void *em_fn(bool weighted, bool smem)
+static const void *em_fn(EmVariant v)
 {
-    return weighted ? (smem ? (const void *)em_kernel<true, true> : (const void *)em_kernel<true, false>)
-                    : (smem ? (const void *)em_kernel<false, true> : (const void *)em_kernel<false, false>);
+    if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true> : (const void *)em_kernel<true, false, true, true>;
+    if (v.mlp) return v.smem ? (const void *)em_kernel<true, true, true, false> : (const void *)em_kernel<true, false, true, false>;
+    if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false> : (const void *)em_kernel<true, false, false, false>;
+    return v.smem ? (const void *)em_kernel<false, true, false, false> : (const void *)em_kernel<false, false, false, false>;
 }
 
-// Opt in to the dynamic shared memory the table needs (outside any stream
-// capture), then report resident blocks per SM for this shape.
-int em_occupancy(bool weighted, bool smem, int block, size_t smem_bytes)
+// Opt in to the dynamic shared memory the table (and proposal) need, outside
+// any stream capture, then report resident blocks per SM for this shape.
+int em_occupancy(EmVariant v, int block, size_t smem_bytes)
 {
-    const void *f = em_fn(weighted, smem);
+    const void *f = em_fn(v);
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
         return 0;
     int nb = 0;
@@ -291,17 +385,10 @@ int em_occupancy(bool weighted, bool smem, int block, size_t smem_bytes)
 
 // Launch only (safe inside stream capture): em_occupancy() must have been
 // called for this shape first.
-cudaError_t em_launch(const EmParams &p, bool weighted, bool smem, int grid, int block,
-                      size_t smem_bytes, cudaStream_t s)
+cudaError_t em_launch(const EmParams &p, EmVariant v, int grid, int block, size_t smem_bytes, cudaStream_t s)
 {
-    if (weighted) {
-        if (smem) em_kernel<true, true><<<grid, block, smem_bytes, s>>>(p);
-        else em_kernel<true, false><<<grid, block, smem_bytes, s>>>(p);
-    } else {
-        if (smem) em_kernel<false, true><<<grid, block, smem_bytes, s>>>(p);
-        else em_kernel<false, false><<<grid, block, smem_bytes, s>>>(p);
-    }
-    return cudaGetLastError();
+    void *args[] = {const_cast<EmParams *>(&p)};
+    return cudaLaunchKernel(em_fn(v), dim3(grid), dim3(block), args, smem_bytes, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -79,6 +79,21 @@ class fpt_hist(C.Structure):
                 ("ess_tail", C.c_double), ("p_tail", C.c_double), ("log_max_w", C.c_double)]
 
 
+class fpt_adam(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("clip", C.c_float), ("step", C.c_int32)]
+
+
+class fpt_train_stats(C.Structure):
+    _fields_ = [("loss", C.c_double), ("mean_Y", C.c_double), ("mean_N", C.c_double),
+                ("n_traj", C.c_int64), ("n_records", C.c_int64), ("n_capped", C.c_int64),
+                ("grad_norm", C.c_double)]
+
+
+FPT_MLP_PARAMS = 4546
+FPT_MLP_BLOB_BYTES = 11808
+
+
 # Every function the header declares, with its ctypes signature.
 _SIGNATURES = {
     "fpt_init_model": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(fpt_model), C.c_int32, C.c_int32]),
@@ -101,6 +116,14 @@ _SIGNATURES = {
     "fpt_histogram_data": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double,
                                      C.POINTER(fpt_hist), C.c_void_p]),
+    "fpt_mlp_pack": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fpt_mlp_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                               C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fpt_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                               C.c_float, C.c_void_p, C.c_void_p]),
+    "fpt_mlp_train_round": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_double,
+                                      C.c_double, C.POINTER(fpt_adam), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(fpt_train_stats), C.c_void_p]),
     "fpt_destroy": (None, [C.c_void_p]),
     "fpt_last_error": (C.c_char_p, [C.c_void_p]),
     "fpt_version": (C.c_char_p, []),
@@ -154,12 +177,17 @@ def _ptr(buf) -> Optional[int]:
     raise TypeError(f"unsupported buffer type {type(buf)}")
 
 
+CUDA_STREAM_LEGACY = 0x1      # cudaStreamLegacy: the legacy default stream
+
+
 def _stream(stream) -> Optional[int]:
+    """None -> the context's private stream; a torch stream (or handle) ->
+    that stream. Handle 0 (torch's default stream) is the legacy default
+    stream, which the ABI spells cudaStreamLegacy (NULL means "context")."""
     if stream is None:
         return None
-    if isinstance(stream, int):
-        return stream
-    return int(stream.cuda_stream)
+    h = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    return h if h != 0 else CUDA_STREAM_LEGACY
 
 
 def model_struct(m) -> fpt_model:
@@ -350,3 +378,63 @@ def fpt_histogram_data(ctx: Context, nsteps, logw, status, dN: float, N_lo: floa
         res[k] = getattr(h, k)
     res["db"] = (N_hi - N_lo) / n_bins
     return res
+
+
+def fpt_mlp_pack(ctx: Context, params, blob, stream=None):
+    """Pack fp32 parameters (host numpy/torch or device tensor) into the
+    device weight blob (a CUDA tensor of >= FPT_MLP_BLOB_BYTES bytes)."""
+    if isinstance(params, np.ndarray):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().fpt_mlp_pack(ctx.handle, _ptr(params), _ptr(blob), _stream(stream)), ctx.handle)
+
+
+def fpt_mlp_eval(ctx: Context, blob, s, tan_t, alpha_max: float, stream=None):
+    """alpha and raw outputs of the network at normalised inputs s (n x 3)."""
+    s = np.ascontiguousarray(s, dtype=np.float32)
+    t = np.ascontiguousarray(tan_t, dtype=np.float32)
+    n = len(t)
+    alpha = np.zeros(n, np.float32)
+    o = np.zeros((n, 2), np.float32)
+    _check(load().fpt_mlp_eval(ctx.handle, _ptr(blob), _ptr(s), _ptr(t), n, alpha_max, _ptr(alpha),
+                               _ptr(o), _stream(stream)), ctx.handle)
+    return alpha, o
+
+
+def fpt_mlp_grad(ctx: Context, params, s, tan_t, dalpha, alpha_max: float, stream=None):
+    """sum_r dalpha_r d alpha(s_r, t_r)/d theta, canonical fp32 order."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    s = np.ascontiguousarray(s, dtype=np.float32)
+    t = np.ascontiguousarray(tan_t, dtype=np.float32)
+    d = np.ascontiguousarray(dalpha, dtype=np.float32)
+    g = np.zeros(FPT_MLP_PARAMS, np.float32)
+    _check(load().fpt_mlp_grad(ctx.handle, _ptr(params), _ptr(s), _ptr(t), _ptr(d), len(t), alpha_max,
+                               _ptr(g), _stream(stream)), ctx.handle)
+    return g
+
+
+def fpt_mlp_train_round(ctx: Context, run: fpt_run_desc, chunk: int, lam: float, N_cut: float,
+                        adam: dict, params, adam_m, adam_v, blob, stream=None) -> dict:
+    a = fpt_adam(lr=adam["lr"], beta1=adam.get("beta1", 0.9), beta2=adam.get("beta2", 0.999),
+                 eps=adam.get("eps", 1e-8), clip=adam.get("clip", 0.0), step=adam["step"])
+    st = fpt_train_stats()
+    _check(load().fpt_mlp_train_round(ctx.handle, C.byref(run), chunk, lam, N_cut, C.byref(a),
+                                      _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(blob), C.byref(st),
+                                      _stream(stream)), ctx.handle)
+    return {k: getattr(st, k) for k, _ in fpt_train_stats._fields_}
+
+
+def canonical_params(p: dict) -> np.ndarray:
+    """Flatten {W1, b1, W2, b2, W3, b3} into the canonical fp32 vector."""
+    return np.concatenate([np.asarray(p[k], np.float64).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+                          ).astype(np.float32)
+
+
+def params_dict(v) -> dict:
+    v = np.asarray(v, np.float64)
+    H = 64
+    out, o = {}, 0
+    for k, shape in (("W1", (H, 3)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (2, H)), ("b3", (2,))):
+        size = int(np.prod(shape))
+        out[k] = v[o:o + size].reshape(shape)
+        o += size
+    return out

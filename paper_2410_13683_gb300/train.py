@@ -1,0 +1,63 @@
+"""Training driver of the learned importance-sampling proposal.
+
+Host orchestration only: every round calls fpt_mlp_train_round (generation
+with segment records, loss coefficients, bf16 tensor-core backward, Adam and
+re-packing all run in libfpt.so). Device memory comes from PyTorch.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import fpt
+
+
+@dataclass
+class Proposal:
+    """A trained proposal: fp32 master parameters, the packed bf16 blob and
+    the input normalisation it was trained with."""
+    params: object           # torch CUDA float32 tensor [FPT_MLP_PARAMS]
+    blob: object             # torch CUDA uint8 tensor [FPT_MLP_BLOB_BYTES]
+    shift: tuple
+    scale: tuple
+    segment: int
+    alpha_max: float
+    history: List[dict] = field(default_factory=list)
+
+    def desc(self, model: int, n_traj: int, seed: int, run_id: int, traj_offset: int = 0):
+        return fpt.run_desc(model, n_traj, seed=seed, run_id=run_id, traj_offset=traj_offset,
+                            bias_kind=fpt.FPT_BIAS_MLP, mlp=self.blob, mlp_segment=self.segment,
+                            mlp_shift=self.shift, mlp_scale=self.scale, alpha_max=self.alpha_max)
+
+
+def new_proposal(ctx, init_params: np.ndarray, shift, scale, segment: int = 64, alpha_max: float = 4.0):
+    import torch
+    p = torch.tensor(np.asarray(init_params, np.float32), device="cuda")
+    blob = torch.zeros(fpt.FPT_MLP_BLOB_BYTES, dtype=torch.uint8, device="cuda")
+    fpt.fpt_mlp_pack(ctx, p, blob)
+    torch.cuda.synchronize()
+    return Proposal(p, blob, tuple(float(v) for v in shift), tuple(float(v) for v in scale), segment,
+                    alpha_max)
+
+
+def train(ctx, prop: Proposal, model: int, rounds: int, n_traj: int, seed: int, lam: float,
+          N_cut: Callable[[int], float], lr: float = 3e-3, chunk: Optional[int] = None,
+          clip: float = 0.0, log: Optional[Callable[[dict], None]] = None) -> Proposal:
+    """`rounds` Adam steps of the log-variance loss; round r draws n_traj
+    fresh trajectories (Philox run id = r) from the current proposal."""
+    import torch
+    m = torch.zeros_like(prop.params)
+    v = torch.zeros_like(prop.params)
+    for r in range(rounds):
+        run = prop.desc(model, n_traj, seed=seed, run_id=r)
+        st = fpt.fpt_mlp_train_round(ctx, run, chunk or n_traj, lam, N_cut(r),
+                                     dict(lr=lr, step=r + 1, clip=clip), prop.params, m, v, prop.blob)
+        st["round"] = r
+        st["N_cut"] = N_cut(r)
+        prop.history.append(st)
+        if log:
+            log(st)
+    return prop
