@@ -191,8 +191,12 @@ typedef struct {
     float mlp_shift[3];     /* FPT_BIAS_MLP: input shift                     */
     float mlp_scale[3];     /* FPT_BIAS_MLP: input scale                     */
     float alpha_max;        /* FPT_BIAS_MLP: |alpha| clamp (> 0)             */
-    int32_t pad;
+    int32_t mlp_flags;      /* FPT_BIAS_MLP: FPT_MLP_LOG_X = first input is
+                               ln(max(phi - phi_end, 1e-30)) instead of
+                               phi - phi_end                                 */
 } fpt_run_desc;
+
+enum { FPT_MLP_LOG_X = 1 };
 
 /* Per-trajectory results of one run; each pointer host or device, nullable.
  * Arrays hold n_traj entries in trajectory order. */

@@ -117,7 +117,7 @@ typedef struct {
     int64_t segment;     /* MLP: alpha recomputed every `segment` steps */
     double alpha_max;    /* MLP: |alpha| clamp */
     int32_t round_bf16;  /* MLP: round operands to bfloat16 as the GPU does */
-    int32_t pad;
+    int32_t log_x;       /* MLP: first input ln(max(phi - phi_end, 1e-30)) */
     const double *W1, *b1, *W2, *b2, *W3, *b3;   /* row-major (out, in) */
     double in_shift[3], in_scale[3];             /* input = (s - shift) * scale */
 } oracle_bias;
@@ -195,7 +195,9 @@ void oracle_mlp_forward(const oracle_bias *b, const double s[3], double o[2])
 static double mlp_alpha(const oracle_bias *b, const oracle_model *m,
                         double phi, double pi, int64_t n, double t)
 {
-    double s[3] = {phi - m->phi_end, pi, (double)n * m->dN};
+    double x = phi - m->phi_end;
+    if (b->log_x) x = log(x > 1e-30 ? x : 1e-30);
+    double s[3] = {x, pi, (double)n * m->dN};
     double o[2];
     oracle_mlp_forward(b, s, o);
     double a = (o[0] + t * o[1]) / sqrt(1.0 + t * t);
@@ -246,7 +248,9 @@ static void one_trajectory(const oracle_model *m, const oracle_table *tab,
             double t = (S != 0.0) ? T / S : 0.0;
             alpha = mlp_alpha(b, m, phi, pi, n, t);
             if (seg && ns < seg->cap) {
-                seg->state[3 * ns + 0] = phi - m->phi_end;
+                double x = phi - m->phi_end;
+                if (b->log_x) x = log(x > 1e-30 ? x : 1e-30);
+                seg->state[3 * ns + 0] = x;
                 seg->state[3 * ns + 1] = pi;
                 seg->state[3 * ns + 2] = (double)n * dN;
                 seg->tan_theta[ns] = t;

@@ -43,7 +43,7 @@ class _Table(C.Structure):
 class _Bias(C.Structure):
     _fields_ = [("kind", C.c_int32), ("hidden", C.c_int32), ("A", C.c_double),
                 ("segment", C.c_int64), ("alpha_max", C.c_double),
-                ("round_bf16", C.c_int32), ("pad", C.c_int32),
+                ("round_bf16", C.c_int32), ("log_x", C.c_int32),
                 ("W1", C.POINTER(C.c_double)), ("b1", C.POINTER(C.c_double)),
                 ("W2", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)),
                 ("W3", C.POINTER(C.c_double)), ("b3", C.POINTER(C.c_double)),
@@ -131,19 +131,20 @@ class MLPBias:
     """FP64 MLP proposal parameters for the oracle (weights kept alive here)."""
 
     def __init__(self, params: dict, segment: int, in_shift, in_scale, alpha_max=20.0,
-                 round_bf16=True):
+                 round_bf16=True, log_x=False):
         self.p = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in params.items()}
         self.segment = int(segment)
         self.in_shift = list(in_shift)
         self.in_scale = list(in_scale)
         self.alpha_max = float(alpha_max)
         self.round_bf16 = bool(round_bf16)
+        self.log_x = bool(log_x)
         self.hidden = self.p["W1"].shape[0]
 
     def struct(self) -> _Bias:
         p = self.p
         return _Bias(kind=2, hidden=self.hidden, A=0.0, segment=self.segment,
-                     alpha_max=self.alpha_max, round_bf16=int(self.round_bf16), pad=0,
+                     alpha_max=self.alpha_max, round_bf16=int(self.round_bf16), log_x=int(self.log_x),
                      W1=_dp(p["W1"]), b1=_dp(p["b1"]), W2=_dp(p["W2"]), b2=_dp(p["b2"]),
                      W3=_dp(p["W3"]), b3=_dp(p["b3"]),
                      in_shift=(C.c_double * 3)(*self.in_shift),
@@ -155,7 +156,7 @@ def bias_struct(A: float = 0.0, mlp: MLPBias | None = None) -> _Bias:
         return mlp.struct()
     z = (C.c_double * 3)(0.0, 0.0, 0.0)
     return _Bias(kind=1 if A != 0.0 else 0, hidden=0, A=float(A), segment=1, alpha_max=0.0,
-                 round_bf16=0, pad=0, in_shift=z, in_scale=z)
+                 round_bf16=0, log_x=0, in_shift=z, in_scale=z)
 
 
 def run(m, resolved, table, seed: int, run_id: int, n: int, traj0: int = 0,

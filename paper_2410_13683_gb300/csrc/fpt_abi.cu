@@ -526,7 +526,9 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
                     return fail(ctx, FPT_E_INVALID, "MLP input shift/scale must be finite");
             if (mlp_run < 0) mlp_run = r;
             const fpt_run_desc &q = runs[mlp_run];
+            if (d.mlp_flags & ~FPT_MLP_LOG_X) return fail(ctx, FPT_E_INVALID, "unknown mlp_flags bits");
             if (d.mlp != q.mlp || d.mlp_segment != q.mlp_segment || d.alpha_max != q.alpha_max ||
+                d.mlp_flags != q.mlp_flags ||
                 std::memcmp(d.mlp_shift, q.mlp_shift, sizeof(q.mlp_shift)) ||
                 std::memcmp(d.mlp_scale, q.mlp_scale, sizeof(q.mlp_scale)))
                 return fail(ctx, FPT_E_INVALID, "all MLP runs of one call must share one proposal");
@@ -568,6 +570,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             rd.mlp = d.mlp;
             for (int k = 0; k < 3; ++k) { rd.shift[k] = d.mlp_shift[k]; rd.scale[k] = d.mlp_scale[k]; }
             rd.alpha_max = d.alpha_max;
+            rd.mlp_flags = d.mlp_flags;
         }
         begin += d.n_traj;
     }

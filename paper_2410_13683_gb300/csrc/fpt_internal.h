@@ -62,7 +62,7 @@ struct RunDev {
     float alpha_max;
     float sqrt_dN;
     float dN;
-    int32_t pad;
+    int32_t mlp_flags;
 };
 
 struct EmParams {

@@ -202,7 +202,9 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
 {
     float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f, tan_t = 0.0f;
     if (live) {
-        in0 = (__fsub_rn(L.x, L.x_c) - pr.shift[0]) * pr.scale[0];
+        const float xv = __fsub_rn(L.x, L.x_c);
+        in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
+        in0 = (in0 - pr.shift[0]) * pr.scale[0];
         in1 = (L.p - pr.shift[1]) * pr.scale[1];
         in2 = ((float)L.n * L.dN - pr.shift[2]) * pr.scale[2];
         float f;

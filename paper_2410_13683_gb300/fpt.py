@@ -27,6 +27,7 @@ FPT_POT_PWLINEAR, FPT_POT_EXP = 0, 1
 FPT_TABLE_DESITTER, FPT_TABLE_BESSEL, FPT_TABLE_USER = 0, 1, 2
 FPT_BIAS_NONE, FPT_BIAS_CONST, FPT_BIAS_MLP = 0, 1, 2
 FPT_TRAJ_PASSED, FPT_TRAJ_CAPPED, FPT_TRAJ_ABORTED = 0, 1, 2
+FPT_MLP_LOG_X = 1
 
 _STATUS_NAMES = {0: "FPT_OK", 1: "FPT_E_INVALID", 2: "FPT_E_CUDA", 3: "FPT_E_NOMEM",
                  4: "FPT_E_TIMEOUT", 5: "FPT_E_STATE", 100: "FPT_W_CAPPED"}
@@ -56,7 +57,7 @@ class fpt_run_desc(C.Structure):
                 ("n_traj", C.c_int64), ("traj_offset", C.c_int64), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("mlp_segment", C.c_int32), ("mlp", C.c_void_p),
                 ("mlp_shift", C.c_float * 3), ("mlp_scale", C.c_float * 3),
-                ("alpha_max", C.c_float), ("pad", C.c_int32)]
+                ("alpha_max", C.c_float), ("mlp_flags", C.c_int32)]
 
 
 class fpt_traj_out(C.Structure):
@@ -311,14 +312,15 @@ def fpt_autotune(ctx: Context, runs: Sequence[fpt_run_desc], fraction: float = 0
 
 def run_desc(model: int = 0, n_traj: int = 0, seed: int = 0, run_id: int = 0, A: float = 0.0,
              traj_offset: int = 0, bias_kind: Optional[int] = None, mlp=None, mlp_segment: int = 0,
-             mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max: float = 0.0):
+             mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max: float = 0.0,
+             mlp_flags: int = 0):
     if bias_kind is None:
         bias_kind = FPT_BIAS_MLP if mlp is not None else (FPT_BIAS_CONST if A != 0.0 else FPT_BIAS_NONE)
     return fpt_run_desc(model=model, bias_kind=bias_kind, A=A, n_traj=n_traj,
                         traj_offset=traj_offset, seed=seed, run_id=run_id,
                         mlp_segment=mlp_segment, mlp=_ptr(mlp),
                         mlp_shift=(C.c_float * 3)(*mlp_shift), mlp_scale=(C.c_float * 3)(*mlp_scale),
-                        alpha_max=alpha_max, pad=0)
+                        alpha_max=alpha_max, mlp_flags=mlp_flags)
 
 
 def fpt_run(ctx: Context, runs: Sequence[fpt_run_desc], out: Optional[Sequence[dict]] = None,
