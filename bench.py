@@ -12,6 +12,11 @@ weighted histogram and its FP64 finalisation. The metric is the effective
 sample size of the tail set T = {N >= N_12} (CCDF(N_12) = 1e-12) per second:
 ESS_T = (sum_T w)^2 / sum_T w^2, summed over all steps and ranks.
 
+The proposal is the learned MLP bias (trained first, untimed, by the
+library's own forward/backward kernels and reported separately); the
+constant-bias proposal (the judge) and direct sampling are measured on the
+same GPU for comparison.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun every rank runs its own trajectory range (weak scaling); the
@@ -47,8 +52,14 @@ TAIL_P = 1e-12
 # stepper (thread instructions): table lookup 10, drift 9, momentum update 4,
 # field increment + compensated add 7, log-weight (Kahan) 5, counter + passage
 # 5, predication 2, Philox4x32-10 (40 per 4 steps) 10, uniforms + Box-Muller
-# (32 per 4 normals) 8. See the design doc.
+# (32 per 4 normals) 8. The learned proposal adds one network evaluation per
+# 64-step segment: 44 mma + 61 fragment loads + 128 SiLU (4 each) + 64 packs +
+# ~40 shuffles/selects per lane = ~760, i.e. 12 per step. See the design doc.
 INSTR_PER_STEP = 60
+INSTR_PER_STEP_MLP = 72
+# Training recipe of the learned proposal (log-variance loss towards
+# e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum).
+TRAIN = dict(rounds=240, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=64, lr0=3e-3, lr_min=3e-4)
 SM_LANES = 128
 
 
@@ -129,13 +140,13 @@ def measured_peaks():
         return {}
 
 
-def roofline(steps_per_launch, launch_ms, sm_count, sm_max_mhz, traffic):
+def roofline(steps_per_launch, launch_ms, sm_count, sm_max_mhz, traffic, instr_per_step):
     """Issue-slot roofline of the stepper: thread instructions per second."""
-    achieved = steps_per_launch * INSTR_PER_STEP / (launch_ms * 1e-3) / 1e12
+    achieved = steps_per_launch * instr_per_step / (launch_ms * 1e-3) / 1e12
     peak = sm_count * SM_LANES * sm_max_mhz * 1e6 / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Tinst/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": "em_kernel<weighted, smem table>",
+            "kernel": "em_kernel<weighted, smem table, MLP>", "instr_per_step": instr_per_step,
             "peak_source": f"{sm_count} SMs x {SM_LANES} lanes x {sm_max_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
 
 
@@ -183,17 +194,37 @@ def reference_arm(args, rank):
     return 0
 
 
+def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
+    """Train the learned proposal (untimed): returns (proposal, seconds)."""
+    import torch
+    x_in = info["phi_in"] - info["phi_end"]
+    p_in = abs(info["pi_in"])
+    v0 = fpt.canonical_params(W.mlp_init(21, out_scale=0.0))
+    prop = TR.new_proposal(ctx, v0, shift=(math.log(x_in), 0.0, 0.0), scale=(0.2, 1.0 / p_in, 0.01),
+                           segment=TRAIN["segment"], alpha_max=TRAIN["alpha_max"], flags=fpt.FPT_MLP_LOG_X)
+    lr = lambda r: TRAIN["lr0"] if r < 20 else max(TRAIN["lr_min"], TRAIN["lr0"] * 0.98 ** (r - 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    TR.train(ctx, prop, 0, rounds=TRAIN["rounds"], n_traj=TRAIN["n_traj"], seed=seed, lam=TRAIN["lam"],
+             N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 16)
+    torch.cuda.synchronize()
+    return prop, time.perf_counter() - t0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-traj", type=int, default=1 << 22, help="trajectories per step per GPU")
+    ap.add_argument("--proposal", default="learned", choices=["learned", "fixed"])
+    ap.add_argument("--n-traj", type=int, default=0, help="trajectories per step per GPU (0: proposal default)")
     ap.add_argument("--ref-traj", type=int, default=1 << 15, help="oracle trajectories per step")
     ap.add_argument("--cpu-traj", type=int, default=1 << 18, help="CPU-baseline sample size")
+    ap.add_argument("--train-rounds", type=int, default=TRAIN["rounds"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / judge / direct legs")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -202,6 +233,8 @@ def main():
     import torch
     import __graft_entry__
     from paper_2410_13683_gb300 import fpt
+    from paper_2410_13683_gb300 import shard
+    from paper_2410_13683_gb300 import train as TR
 
     torch.cuda.set_device(local)
     dist = None
@@ -209,35 +242,50 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     __graft_entry__.build()
+    TRAIN["rounds"] = args.train_rounds
     tail = load_tail()
-    N_tail, A = tail["N_12"], tail["A"]
+    N_tail, A_judge = tail["N_12"], tail["A"]
     m = usr_model()
-    n = args.n_traj
+    learned = args.proposal == "learned"
+    n = args.n_traj or ((1 << 20) if learned else (1 << 22))
     seed = 20260
     dev = torch.cuda.current_device()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     ctx = fpt.fpt_init_model([m], device=dev)
     S_tab, T_tab = fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
+    info = fpt.fpt_model_get_info(ctx, 0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    off = shard.shard_offset(n, rank)
 
-    def desc(step):
-        return fpt.run_desc(0, n, seed=seed, run_id=step, A=A, traj_offset=rank * n)
+    train_info = None
+    prop = None
+    if learned:
+        prop, train_s = train_proposal(ctx, fpt, TR, info, N_tail)
+        h = prop.history
+        train_info = {"rounds": len(h), "seconds": round(train_s, 2), "traj_per_round": TRAIN["n_traj"],
+                      "lambda": TRAIN["lam"], "N_cut": N_tail, "final_loss": round(h[-1]["loss"], 3),
+                      "first_loss": round(h[0]["loss"], 3), "segment": TRAIN["segment"],
+                      "alpha_max": TRAIN["alpha_max"], "inputs": "(ln x, pi, N)"}
+
+    def desc(step, nn=n, offset=off):
+        if learned:
+            return prop.desc(0, nn, seed=seed, run_id=step, traj_offset=offset)
+        return fpt.run_desc(0, nn, seed=seed, run_id=step, A=A_judge, traj_offset=offset)
 
     if args.no_autotune:
         launch = fpt.fpt_get_launch(ctx)
     else:
         launch = fpt.fpt_autotune(ctx, [desc(10_000)], fraction=0.25)
 
-    def one_step(step, ev=None):
+    def one_step(step, ev=None, d=None):
         if ev is not None:
             ev[0].record(stream)
-        fpt.fpt_run(ctx, [desc(step)], stream=stream)
+        fpt.fpt_run(ctx, [d or desc(step)], stream=stream)
         if ev is not None:
             ev[1].record(stream)
         h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
-        sw = h["p_tail"] * h["n_total"]
-        sw2 = sw * sw / h["ess_tail"] if h["ess_tail"] > 0 else 0.0
+        sw, sw2 = shard.tail_sums(h)
         steps = (h["N_mean"] * h["n_passed"] + h["n_capped"] * m.max_steps * m.dN) / m.dN
         return sw, sw2, steps
 
@@ -270,47 +318,61 @@ def main():
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
-        s = torch.tensor([sw_tot, sw2_tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(s)
-        sw_tot, sw2_tot = float(s[0]), float(s[1])
-    ess_total = sw_tot * sw_tot / sw2_tot if sw2_tot > 0 else 0.0
+    sw_tot, sw2_tot = shard.merge_tail_sums(sw_tot, sw2_tot, dist, device="cuda")
+    ess_total = shard.ess_of(sw_tot, sw2_tot)
     value = ess_total / elapsed
 
-    # end to end through the public API with host buffers: the noise table
-    # uploaded from pinned host memory, descriptors from the host, the
-    # histogram read back to host memory, timed on the host clock
-    S_pin = torch.from_numpy(S_tab).pin_memory().numpy()
-    T_pin = torch.from_numpy(T_tab).pin_memory().numpy()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sw_e = sw2_e = 0.0
-    for k in range(args.steps):
-        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, len(S_pin), 1.0, float("nan"), float("nan"), S_pin, T_pin)
-        fpt.fpt_run(ctx, [desc(500_000 + k)], stream=stream)
-        h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
-        sw = h["p_tail"] * h["n_total"]
-        sw_e += sw
-        sw2_e += sw * sw / h["ess_tail"] if h["ess_tail"] > 0 else 0.0
-    torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
-    e2e_val = (sw_e * sw_e / sw2_e if sw2_e > 0 else 0.0) / e2e_t * world
-    h2d = len(S_pin) * 16 + 128
-    d2h = (10 * 512 + 16) * 8
-
-    # direct sampling on the same GPU: ESS_T = n * 1e-12 in expectation
-    nd = 1 << 22
-    ddesc = [fpt.run_desc(0, nd, seed=seed + 1, run_id=0)]
-    fpt.fpt_run(ctx, ddesc, stream=stream)
-    fpt.fpt_sync(ctx)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(3):
-        fpt.fpt_run(ctx, [fpt.run_desc(0, nd, seed=seed + 1, run_id=k + 1)], stream=stream)
-        fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    direct_traj_s = 3 * nd / (e0.elapsed_time(e1) * 1e-3)
-    direct_ess_s = direct_traj_s * TAIL_P * world
+    extras = {}
+    if not args.no_extras:
+        # end to end through the public API with host buffers: the noise table
+        # from pinned host memory, descriptors from the host, the histogram read
+        # back to host memory, all on the host clock
+        S_pin = torch.from_numpy(S_tab).pin_memory().numpy()
+        T_pin = torch.from_numpy(T_tab).pin_memory().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sw_e = sw2_e = 0.0
+        for k in range(args.steps):
+            fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, len(S_pin), 1.0, float("nan"), float("nan"),
+                                S_pin, T_pin)
+            sw, sw2, _ = one_step(500_000 + k)
+            sw_e += sw
+            sw2_e += sw2
+        torch.cuda.synchronize()
+        e2e_t = time.perf_counter() - t0
+        sw_e, sw2_e = shard.merge_tail_sums(sw_e, sw2_e, dist, device="cuda")
+        extras["e2e"] = {"value": shard.ess_of(sw_e, sw2_e) / e2e_t, "unit": UNIT,
+                         "h2d_bytes_per_step": len(S_pin) * 16 + 128 + (fpt.FPT_MLP_BLOB_BYTES if learned else 0),
+                         "d2h_bytes_per_step": (10 * 512 + 16) * 8}
+        # the constant-bias judge (the method without the learned part)
+        nj = 1 << 22
+        jd = lambda k: fpt.run_desc(0, nj, seed=seed + 2, run_id=k, A=A_judge, traj_offset=rank * nj)
+        one_step(0, d=jd(900))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        swj = sw2j = 0.0
+        for k in range(3):
+            sw, sw2, _ = one_step(0, d=jd(k))
+            swj += sw
+            sw2j += sw2
+        e1.record(stream)
+        torch.cuda.synchronize()
+        swj, sw2j = shard.merge_tail_sums(swj, sw2j, dist, device="cuda")
+        judge = shard.ess_of(swj, sw2j) / (e0.elapsed_time(e1) * 1e-3)
+        extras["fixed_bias"] = {"A": A_judge, "n_traj_per_step": nj, "ess_tail_per_s": judge}
+        # direct sampling on the same GPU: ESS_T = n * 1e-12 in expectation
+        nd = 1 << 22
+        fpt.fpt_run(ctx, [fpt.run_desc(0, nd, seed=seed + 1, run_id=0, traj_offset=rank * nd)], stream=stream)
+        fpt.fpt_sync(ctx)
+        e0.record(stream)
+        for k in range(3):
+            fpt.fpt_run(ctx, [fpt.run_desc(0, nd, seed=seed + 1, run_id=k + 1, traj_offset=rank * nd)],
+                        stream=stream)
+            fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        direct_traj_s = 3 * nd / (e0.elapsed_time(e1) * 1e-3)
+        extras["direct"] = {"traj_per_s": direct_traj_s * world, "ess_tail_per_s": direct_traj_s * TAIL_P * world}
 
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
@@ -322,35 +384,45 @@ def main():
         except Exception:
             traffic = None
     mean_run_ms = float(np.mean(run_ms))
-    rl = roofline(steps_tot / args.steps, mean_run_ms, sm_count, sm_max, traffic)
+    rl = roofline(steps_tot / args.steps, mean_run_ms, sm_count, sm_max, traffic,
+                  INSTR_PER_STEP_MLP if learned else INSTR_PER_STEP)
+    if not learned:
+        rl["kernel"] = "em_kernel<weighted, smem table>"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "usr_fixed_bias_tail", "model": "piecewise-linear USR, V0=2e-10 a+=1e-3 a-=1e-6",
-                       "proposal": f"constant A={A}", "n_traj_per_step_per_gpu": n, "N_tail": N_tail,
+            "config": {"workload": "usr_learned_tail" if learned else "usr_fixed_bias_tail",
+                       "model": "piecewise-linear USR, V0=2e-10 a+=1e-3 a-=1e-6, phi*=1",
+                       "proposal": "learned MLP 3-64-64-2 (bf16)" if learned else f"constant A={A_judge}",
+                       "n_traj_per_step_per_gpu": n, "N_tail": N_tail,
                        "table_points": W.USR_TABLE.n_points, "dN": m.dN, "max_steps": m.max_steps,
-                       "l2": "per-step inputs are generated in-kernel; working set (64 KB table) stays on chip",
+                       "l2": "inputs are generated in-kernel; the 64 KB table and 12 KB weights stay in shared memory",
                        "launch": launch},
             "roofline": rl,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "ess_tail_total": ess_total,
             "em_steps_per_step": steps_tot / args.steps,
             "em_steps_per_s": steps_tot / (sum(run_ms) * 1e-3),
-            "em_launch_ms": mean_run_ms,
-            "direct": {"traj_per_s": direct_traj_s, "ess_tail_per_s": direct_ess_s},
-            "gain_vs_direct": value / direct_ess_s if direct_ess_s > 0 else None}
+            "em_launch_ms": mean_run_ms}
+    if train_info:
+        line["train"] = train_info
+    line.update(extras)
+    if "direct" in extras and extras["direct"]["ess_tail_per_s"] > 0:
+        line["gain_vs_direct"] = value / extras["direct"]["ess_tail_per_s"]
+    if "fixed_bias" in extras and extras["fixed_bias"]["ess_tail_per_s"] > 0:
+        line["gain_vs_fixed_bias"] = value / extras["fixed_bias"]["ess_tail_per_s"]
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import tables as OT
         res = OT.resolve(m)
         tab = OT.bessel_table(m, res, W.USR_TABLE.n_points, W.USR_TABLE.sigma, processes=os.cpu_count())
-        e, dt, cores, nsteps = cpu_oracle_sample((m, res, tab), A, N_tail, args.cpu_traj)
+        e, dt, cores, nsteps = cpu_oracle_sample((m, res, tab), A_judge, N_tail, args.cpu_traj)
         line["cpu_baseline"] = {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{args.cpu_traj} trajectories of the same workload "
-                                          f"({nsteps} Euler-Maruyama steps, {dt:.1f} s)"}
+                                "sample": f"{args.cpu_traj} trajectories of the same workload with the "
+                                          f"constant-bias proposal A={A_judge} ({nsteps} Euler-Maruyama "
+                                          f"steps, {dt:.1f} s)"}
     fpt.fpt_sync(ctx)
     ctx.close()
     if rank == 0:

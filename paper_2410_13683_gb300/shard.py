@@ -1,0 +1,40 @@
+"""Trajectory-range sharding across ranks and the merge of tail statistics.
+
+Philox is keyed by the global trajectory id, so rank r running ids
+[r n, (r + 1) n) reproduces exactly the trajectories a single process would run
+for those ids. The only exchange is a sum of the tail weight sums
+(sum_T w, sum_T w^2), from which the merged effective sample size follows.
+"""
+from __future__ import annotations
+
+import math
+
+
+def shard_offset(n_per_rank: int, rank: int) -> int:
+    """First global trajectory id of `rank` (weak scaling: n_per_rank each)."""
+    if n_per_rank < 0 or rank < 0:
+        raise ValueError("n_per_rank and rank must be non-negative")
+    if (rank + 1) * n_per_rank > (1 << 32):
+        raise ValueError("trajectory ids must stay below 2^32")
+    return rank * n_per_rank
+
+
+def tail_sums(hist: dict) -> tuple:
+    """(sum_T w, sum_T w^2) of one histogram result (fpt_histogram dict)."""
+    sw = hist["p_tail"] * hist["n_total"]
+    sw2 = sw * sw / hist["ess_tail"] if hist["ess_tail"] > 0 else 0.0
+    return sw, sw2
+
+
+def ess_of(sw: float, sw2: float) -> float:
+    return sw * sw / sw2 if sw2 > 0 else 0.0
+
+
+def merge_tail_sums(sw: float, sw2: float, dist=None, device=None) -> tuple:
+    """All-reduce (sum) of the tail sums over the default process group."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return sw, sw2
+    import torch
+    t = torch.tensor([sw, sw2], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t[0]), float(t[1])

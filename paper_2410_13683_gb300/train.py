@@ -47,19 +47,24 @@ def new_proposal(ctx, init_params: np.ndarray, shift, scale, segment: int = 64, 
 
 
 def train(ctx, prop: Proposal, model: int, rounds: int, n_traj: int, seed: int, lam: float,
-          N_cut: Callable[[int], float], lr: float = 3e-3, chunk: Optional[int] = None,
-          clip: float = 0.0, log: Optional[Callable[[dict], None]] = None) -> Proposal:
+          N_cut: Callable[[int], float], lr=3e-3, chunk: Optional[int] = None,
+          clip: float = 0.0, log: Optional[Callable[[dict], None]] = None,
+          first_round: int = 0) -> Proposal:
     """`rounds` Adam steps of the log-variance loss; round r draws n_traj
-    fresh trajectories (Philox run id = r) from the current proposal."""
+    fresh trajectories (Philox run id = r) from the current proposal. `lr`
+    is a number or a function of the round."""
     import torch
-    m = torch.zeros_like(prop.params)
-    v = torch.zeros_like(prop.params)
-    for r in range(rounds):
+    if not hasattr(prop, "_adam"):
+        prop._adam = (torch.zeros_like(prop.params), torch.zeros_like(prop.params))
+    m, v = prop._adam
+    for r in range(first_round, first_round + rounds):
         run = prop.desc(model, n_traj, seed=seed, run_id=r)
+        lr_r = lr(r) if callable(lr) else lr
         st = fpt.fpt_mlp_train_round(ctx, run, chunk or n_traj, lam, N_cut(r),
-                                     dict(lr=lr, step=r + 1, clip=clip), prop.params, m, v, prop.blob)
+                                     dict(lr=lr_r, step=r + 1, clip=clip), prop.params, m, v, prop.blob)
         st["round"] = r
         st["N_cut"] = N_cut(r)
+        st["lr"] = lr_r
         prop.history.append(st)
         if log:
             log(st)
