@@ -352,6 +352,38 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
                                float *adam_m, float *adam_v, void *blob,
                                fpt_train_stats *stats, void *cuda_stream);
 
+/*
+ * The weighted histogram of fpt_histogram_data for callers that cannot
+ * allocate device memory: code that runs where cudaMalloc is not allowed or
+ * not wanted -- inside another library's allocation-free region, on a stream
+ * being captured by an application that forbids allocation, or under an
+ * allocator that owns all device memory. The paper has no counterpart; this is
+ * an interface variant, not a step of the method.
+ *
+ * No context, no allocation: the scratch (per-bin maxima, jackknife moments,
+ * scalars; about 1.3 MB) is a fixed array inside the library that every GPU
+ * loading the library holds until the process exits. The call runs on the
+ * calling thread's current device; the first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * The array is cleared at the start of every call, and all calls share it:
+ * calls whose work overlaps on the GPU (different streams, or different
+ * threads without ordering) race and give wrong results.
+ *
+ * Inputs: nsteps, logw, status (device, n entries; status as FPT_TRAJ_*),
+ * dN, bins as in fpt_histogram (1 <= n_bins <= FPT_NOALLOC_MAX_BINS), N_tail.
+ * Output: `out`, device, FPT_HIST_OUT_DOUBLES(n_bins) doubles: ten arrays of
+ * n_bins (count, log_sum_w, log_sum_w2, sum_lw, sum_lw2, pdf, se_w, pdf_ln,
+ * se_ln, se_jk) then 16 scalars (n_total, n_passed, n_under, n_over, n_capped,
+ * n_tail, N_mean, N_mean_w, ess_tail, p_tail, log_max_w, 0...). Asynchronous
+ * on cuda_stream (NULL: the legacy default stream). Errors: FPT_E_INVALID for
+ * bad sizes (message in fpt_last_error(NULL)), FPT_E_CUDA for launch errors.
+ */
+#define FPT_NOALLOC_MAX_BINS 1024
+#define FPT_HIST_OUT_DOUBLES(n_bins) (10 * (n_bins) + 16)
+fpt_status fpt_histogram_noalloc(const int32_t *nsteps, const double *logw, const uint8_t *status,
+                                 int64_t n, double dN, double N_lo, double N_hi, int32_t n_bins,
+                                 double N_tail, double *out, void *cuda_stream);
+
 /* Release everything the context owns. NULL is allowed. */
 void fpt_destroy(fpt_ctx *ctx);
 

@@ -1046,6 +1046,36 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
     return FPT_OK;
 }
 
+fpt_status fpt_histogram_noalloc(const int32_t *nsteps, const double *logw, const uint8_t *status,
+                                 int64_t n, double dN, double N_lo, double N_hi, int32_t n_bins,
+                                 double N_tail, double *out, void *cuda_stream)
+{
+    if (!nsteps || !logw || !status || !out || n < 1)
+        return fail(nullptr, FPT_E_INVALID, "need n >= 1, three input arrays and an output array");
+    if (n_bins < 1 || n_bins > kNoAllocMaxBins)
+        return fail(nullptr, FPT_E_INVALID, "n_bins out of [1, FPT_NOALLOC_MAX_BINS = 1024]");
+    if (!(dN > 0) || !std::isfinite(dN)) return fail(nullptr, FPT_E_INVALID, "dN must be positive");
+    if (!(N_hi > N_lo) || !std::isfinite(N_lo) || !std::isfinite(N_hi))
+        return fail(nullptr, FPT_E_INVALID, "need finite N_lo < N_hi");
+    if (!std::isnan(N_tail) && !std::isfinite(N_tail)) return fail(nullptr, FPT_E_INVALID, "N_tail must be finite or NaN");
+    HistParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nsteps = nsteps;
+    p.logw = logw;
+    p.status = status;
+    p.unit_begin = 0;
+    p.n = n;
+    p.dN = dN;
+    p.N_lo = N_lo;
+    p.db = (N_hi - N_lo) / n_bins;
+    p.N_tail = N_tail;
+    p.n_bins = n_bins;
+    p.chunk = 4096;
+    cudaError_t e = hist_noalloc_launch(p, out, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "fpt_histogram_noalloc");
+    return FPT_OK;
+}
+
 void fpt_destroy(fpt_ctx *ctx)
 {
     if (!ctx) return;

@@ -30,6 +30,7 @@ constexpr int kMaxModels = 64;
 constexpr int kMaxTablePoints = 8192;
 constexpr int kJackknife = 32;       // jackknife blocks of the histogram
 constexpr int kMaxBins = 4096;
+constexpr int kNoAllocMaxBins = 1024;   // fpt_histogram_noalloc
 constexpr int kMlpHidden = 64;
 
 // Model constants in the shifted coordinate x = phi - phi_end (FP32).
@@ -135,6 +136,8 @@ cudaError_t mlp_adam_launch(float *P, const float *G, float *m, float *v, int n,
                             float eps, int step, float clip, cudaStream_t s);
 size_t mlp_bwd_smem();
 cudaError_t hist_launch(const HistParams &p, double *out, cudaStream_t s);
+cudaError_t hist_noalloc_launch(HistParams p, double *out, cudaStream_t s);
+size_t hist_noalloc_scratch_bytes();
 cudaError_t n_of_steps_launch(const int32_t *nsteps, long long n, double dN, double *N,
                               cudaStream_t s);
 

@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace fpt_dev {
 
 // ---------------------------------------------------------------------------
@@ -627,6 +629,56 @@ cudaError_t hist_launch(const HistParams &p, double *out, cudaStream_t s)
     if ((e = cudaGetLastError())) return e;
     hist_finalize_kernel<<<1, 128, 0, s>>>(p, out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Histogram without allocation: the scratch lives in a file-scope device array
+// ---------------------------------------------------------------------------
+// Layout of the array: per-bin maxima (n_bins + 2 keys), then the jackknife
+// moments (kJackknife x n_bins x 5 doubles), then the scalars (kJackknife x 16).
+constexpr size_t kNoAllocKeyBytes = ((sizeof(unsigned long long) * (kNoAllocMaxBins + 2) + 255) / 256) * 256;
+constexpr size_t kNoAllocMomBytes = sizeof(double) * (size_t)kJackknife * kNoAllocMaxBins * 5;
+constexpr size_t kNoAllocScalBytes = sizeof(double) * kJackknife * 16;
+constexpr size_t kNoAllocBytes = kNoAllocKeyBytes + kNoAllocMomBytes + kNoAllocScalBytes;
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_hist_scratch[kNoAllocBytes];
+
+size_t hist_noalloc_scratch_bytes() { return kNoAllocBytes; }
+
+// Device address of the array, looked up once per device with that device
+// current (host code must not use the symbol itself as an address).
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_ptr[64] = {};
+
+static cudaError_t noalloc_scratch(unsigned char **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_hist_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t hist_noalloc_launch(HistParams p, double *out, cudaStream_t s)
+{
+    if (p.n_bins < 1 || p.n_bins > kNoAllocMaxBins) return cudaErrorInvalidValue;
+    unsigned char *base = nullptr;
+    cudaError_t e = noalloc_scratch(&base);
+    if (e != cudaSuccess) return e;
+    p.maxkey = reinterpret_cast<unsigned long long *>(base);
+    p.mom = reinterpret_cast<double *>(base + kNoAllocKeyBytes);
+    p.scal = reinterpret_cast<double *>(base + kNoAllocKeyBytes + kNoAllocMomBytes);
+    // hist_launch clears the maxima, moments and scalars before it bins
+    return hist_launch(p, out, s);
 }
 
 __global__ void n_of_steps_kernel(const int32_t *nsteps, long long n, double dN, double *N)

@@ -125,6 +125,9 @@ _SIGNATURES = {
     "fpt_mlp_train_round": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_double,
                                       C.c_double, C.POINTER(fpt_adam), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(fpt_train_stats), C.c_void_p]),
+    "fpt_histogram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                        C.c_double, C.c_double, C.c_int32, C.c_double, C.c_void_p,
+                                        C.c_void_p]),
     "fpt_destroy": (None, [C.c_void_p]),
     "fpt_last_error": (C.c_char_p, [C.c_void_p]),
     "fpt_version": (C.c_char_p, []),
@@ -440,3 +443,32 @@ def params_dict(v) -> dict:
         out[k] = v[o:o + size].reshape(shape)
         o += size
     return out
+
+
+FPT_NOALLOC_MAX_BINS = 1024
+
+
+def hist_out_doubles(n_bins: int) -> int:
+    return 10 * n_bins + 16
+
+
+def fpt_histogram_noalloc(nsteps, logw, status, dN: float, N_lo: float, N_hi: float, n_bins: int,
+                          out, N_tail: float = NAN, stream=None) -> int:
+    """Allocation-free histogram of device arrays into the device buffer
+    `out` (hist_out_doubles(n_bins) doubles). Asynchronous on `stream`."""
+    st = load().fpt_histogram_noalloc(_ptr(nsteps), _ptr(logw), _ptr(status), int(len(nsteps)), dN, N_lo,
+                                      N_hi, n_bins, N_tail, _ptr(out), _stream(stream))
+    return _check(st)
+
+
+def unpack_hist(buf, n_bins: int) -> dict:
+    """Split the packed histogram output into the fpt_histogram dict layout."""
+    b = np.asarray(buf, dtype=np.float64)
+    res = {}
+    for i, k in enumerate(HIST_ARRAYS):
+        v = b[i * n_bins:(i + 1) * n_bins]
+        res[k] = v.astype(np.int64) if k == "count" else v.copy()
+    sc = b[10 * n_bins:]
+    for i, k in enumerate(HIST_SCALARS):
+        res[k] = int(sc[i]) if k.startswith("n_") else float(sc[i])
+    return res
