@@ -52,15 +52,20 @@ __device__ __forceinline__ float sqrt_approx(float v)
 }
 
 // Two standard normals from two Philox words: 23-bit uniforms
-// u = ((r >> 9) + 0.5) 2^-23 (exact in FP32), then Box-Muller
+// u = ((r >> 9) + 0.5) 2^-23, built from the mantissa bits (1 + (r >> 9) 2^-23
+// minus (1 - 2^-24), exact by Sterbenz), then Box-Muller
 // z0 = rho cos(2 pi u1), z1 = rho sin(2 pi u1), rho = sqrt(-2 ln u0); the
 // angle is evaluated as 2 pi u1 - pi, inside the accurate range of the
 // hardware sine/cosine, and the signs restored.
+__device__ __forceinline__ float uniform23(uint32_t r)
+{
+    return __int_as_float(0x3f800000u | (r >> 9)) - 0.99999994039535522f;   // 1 - 2^-24
+}
+
 __device__ __forceinline__ void box_muller(uint32_t r0, uint32_t r1, float &z0, float &z1)
 {
-    const float s = 1.0f / 8388608.0f;
-    const float u0 = fmaf((float)(r0 >> 9), s, 0.5f * s);
-    const float u1 = fmaf((float)(r1 >> 9), s, 0.5f * s);
+    const float u0 = uniform23(r0);
+    const float u1 = uniform23(r1);
     const float rho = sqrt_approx(fmaxf(-2.0f * __logf(u0), 0.0f));
     float sn, cs;
     __sincosf(fmaf(u1, 6.28318530717958648f, -3.14159265358979324f), &sn, &cs);
@@ -99,7 +104,7 @@ struct Lane {                // per-thread trajectory state and its constants
     float cb, half_cb2, dN, sqrt_dN;
     float x_star, a_plus, a_minus, b_plus, b_minus;
     float u_scale, u_shift, u_max;
-    int i_max, tbase;
+    int tbase;
     bool mlp;
     long long unit;
 };
@@ -137,7 +142,6 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.u_scale = m.u_scale;
     L.u_shift = m.u_shift;
     L.u_max = (float)(m.M - 1);
-    L.i_max = m.M - 2;
     L.tbase = m.table_offset;
     L.nmax = m.max_steps;
     L.x = m.x_in;
@@ -149,13 +153,19 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
 }
 
 // Table entry (S', dS', T', dT') and interpolation weight at the lane's field.
+// u = (phi - phi_lo)/h clamped to [0, M - 1]; the entry index k = round(u - 1/2)
+// comes from adding 1.5 2^23 (round to nearest in the mantissa), so index and
+// weight f = u - k in [0, 1] need no float/int conversion. k = M - 1 happens
+// only at u = M - 1 with f = 0, and entry M - 1 carries zero slopes.
 template <bool SMEM>
 __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restrict__ tab, float &f)
 {
+    const float kMagic = 12582912.0f;                        // 1.5 * 2^23
     float u = fmaf(L.x, L.u_scale, L.u_shift);
     u = fminf(fmaxf(u, 0.0f), L.u_max);
-    const int i = min(__float2int_rz(u), L.i_max);
-    f = u - (float)i;
+    const float t = (u - 0.5f) + kMagic;
+    const int i = __float_as_int(t) - 0x4b400000;
+    f = u - (t - kMagic);
     return SMEM ? tab[i] : __ldg(tab + L.tbase + i);
 }
 
