@@ -210,7 +210,7 @@ typedef struct {
 /* Launch shape. Zero fields take the context defaults (or the autotuned
  * choice). */
 typedef struct {
-    int32_t block;          /* threads per block: 128, 256, 512 or 1024       */
+    int32_t block;          /* threads per block: 128, 192, 256, 384 or 512   */
     int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid)        */
     int32_t check_steps;    /* steps between refill points (multiple of 4)     */
     int32_t use_graph;      /* 1: replay a captured CUDA graph per shape      */
@@ -223,7 +223,7 @@ fpt_status fpt_get_launch(const fpt_ctx *ctx, fpt_launch *launch);
 /*
  * Autotuner: runs `runs` (each n_traj scaled by `fraction`, 0 < fraction <= 1,
  * at least 32 trajectories) under every candidate shape -- block in
- * {128, 256, 512} x check_steps in {8, 32, 128}, resident blocks at maximum
+ * {128, 256, 384, 512} x check_steps in {8, 32, 128}, resident blocks at maximum
  * occupancy -- times each with CUDA events after one warm-up, and keeps the
  * fastest in the context (graph replay and deadline settings are kept).
  * Results of later runs do not depend on the choice. `chosen` (nullable)

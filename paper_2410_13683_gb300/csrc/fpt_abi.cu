@@ -444,8 +444,8 @@ fpt_status fpt_noise_table(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_
 fpt_status fpt_set_launch(fpt_ctx *ctx, const fpt_launch *l)
 {
     if (!ctx || !l) return FPT_E_INVALID;
-    if (l->block && l->block != 128 && l->block != 256 && l->block != 512)
-        return fail(ctx, FPT_E_INVALID, "block must be 128, 256 or 512");
+    if (l->block && l->block != 128 && l->block != 192 && l->block != 256 && l->block != 384 && l->block != 512)
+        return fail(ctx, FPT_E_INVALID, "block must be 128, 192, 256, 384 or 512");
     if (l->blocks_per_sm < 0 || l->blocks_per_sm > 16) return fail(ctx, FPT_E_INVALID, "blocks_per_sm out of [0, 16]");
     if (l->check_steps < 0 || (l->check_steps % 4) || l->check_steps > 4096)
         return fail(ctx, FPT_E_INVALID, "check_steps must be a multiple of 4 in [4, 4096]");
@@ -841,7 +841,7 @@ fpt_status fpt_autotune(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, 
     fpt_launch best = keep;
     float best_ms = -1.0f;
     fpt_status st = FPT_OK;
-    for (int block : {128, 256, 512}) {
+    for (int block : {128, 256, 384, 512}) {
         for (int check : {8, 32, 128}) {
             ctx->launch.block = block;
             ctx->launch.blocks_per_sm = 0;

@@ -85,49 +85,46 @@ __device__ __forceinline__ void mlp_forward_warp(const uint2 *tiles, const float
         // layer-1 A fragment: row r, columns (2t, 2t+1) of (s0, s1, s2, 0, ..., 0)
         const uint32_t a0 = pack_bf16x2(t == 0 ? x0 : (t == 1 ? z0 : 0.0f), t == 0 ? y0 : 0.0f);
         const uint32_t a1 = pack_bf16x2(t == 0 ? x1 : (t == 1 ? z1 : 0.0f), t == 0 ? y1 : 0.0f);
+        // layer 1, two N tiles at a time -> the four K tiles of layer 2's A operand
         uint32_t A[4][4];
-        {
-            float d[8][4];
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const float2 c = *reinterpret_cast<const float2 *>(b1 + 8 * nt + 2 * t);
-                d[nt][0] = c.x; d[nt][1] = c.y; d[nt][2] = c.x; d[nt][3] = c.y;
-                mma_bf16_16816(d[nt], a0, a1, 0u, 0u, tiles[nt * 32 + lane]);
-            }
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                A[kt][0] = pack_bf16x2(silu_f(d[2 * kt][0]), silu_f(d[2 * kt][1]));
-                A[kt][1] = pack_bf16x2(silu_f(d[2 * kt][2]), silu_f(d[2 * kt][3]));
-                A[kt][2] = pack_bf16x2(silu_f(d[2 * kt + 1][0]), silu_f(d[2 * kt + 1][1]));
-                A[kt][3] = pack_bf16x2(silu_f(d[2 * kt + 1][2]), silu_f(d[2 * kt + 1][3]));
-            }
+        for (int kt = 0; kt < 4; ++kt) {
+            float d0[4], d1[4];
+            const float2 c0 = *reinterpret_cast<const float2 *>(b1 + 16 * kt + 2 * t);
+            const float2 c1 = *reinterpret_cast<const float2 *>(b1 + 16 * kt + 8 + 2 * t);
+            d0[0] = c0.x; d0[1] = c0.y; d0[2] = c0.x; d0[3] = c0.y;
+            d1[0] = c1.x; d1[1] = c1.y; d1[2] = c1.x; d1[3] = c1.y;
+            mma_bf16_16816(d0, a0, a1, 0u, 0u, tiles[(2 * kt) * 32 + lane]);
+            mma_bf16_16816(d1, a0, a1, 0u, 0u, tiles[(2 * kt + 1) * 32 + lane]);
+            A[kt][0] = pack_bf16x2(silu_f(d0[0]), silu_f(d0[1]));
+            A[kt][1] = pack_bf16x2(silu_f(d0[2]), silu_f(d0[3]));
+            A[kt][2] = pack_bf16x2(silu_f(d1[0]), silu_f(d1[1]));
+            A[kt][3] = pack_bf16x2(silu_f(d1[2]), silu_f(d1[3]));
         }
-        uint32_t A3[4][4];
-        {
-            const uint2 *t2 = tiles + kTilesL1 * 32;
-            float d[8][4];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const float2 c = *reinterpret_cast<const float2 *>(b2 + 8 * nt + 2 * t);
-                d[nt][0] = c.x; d[nt][1] = c.y; d[nt][2] = c.x; d[nt][3] = c.y;
-#pragma unroll
-                for (int kt = 0; kt < 4; ++kt)
-                    mma_bf16_16816(d[nt], A[kt][0], A[kt][1], A[kt][2], A[kt][3], t2[(nt * 4 + kt) * 32 + lane]);
-            }
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                A3[kt][0] = pack_bf16x2(silu_f(d[2 * kt][0]), silu_f(d[2 * kt][1]));
-                A3[kt][1] = pack_bf16x2(silu_f(d[2 * kt][2]), silu_f(d[2 * kt][3]));
-                A3[kt][2] = pack_bf16x2(silu_f(d[2 * kt + 1][0]), silu_f(d[2 * kt + 1][1]));
-                A3[kt][3] = pack_bf16x2(silu_f(d[2 * kt + 1][2]), silu_f(d[2 * kt + 1][3]));
-            }
-        }
+        // layers 2 and 3 streamed: each pair of layer-2 N tiles is one K tile of
+        // layer 3, consumed as soon as it is formed
+        const uint2 *t2 = tiles + kTilesL1 * 32;
         const uint2 *t3 = tiles + (kTilesL1 + kTilesL2) * 32;
         const float2 c3 = *reinterpret_cast<const float2 *>(b3 + 2 * t);
         float d3[4] = {c3.x, c3.y, c3.x, c3.y};
 #pragma unroll
-        for (int kt = 0; kt < 4; ++kt)
-            mma_bf16_16816(d3, A3[kt][0], A3[kt][1], A3[kt][2], A3[kt][3], t3[kt * 32 + lane]);
+        for (int k3 = 0; k3 < 4; ++k3) {
+            float e0[4], e1[4];
+            const float2 c0 = *reinterpret_cast<const float2 *>(b2 + 16 * k3 + 2 * t);
+            const float2 c1 = *reinterpret_cast<const float2 *>(b2 + 16 * k3 + 8 + 2 * t);
+            e0[0] = c0.x; e0[1] = c0.y; e0[2] = c0.x; e0[3] = c0.y;
+            e1[0] = c1.x; e1[1] = c1.y; e1[2] = c1.x; e1[3] = c1.y;
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                mma_bf16_16816(e0, A[kt][0], A[kt][1], A[kt][2], A[kt][3], t2[((2 * k3) * 4 + kt) * 32 + lane]);
+                mma_bf16_16816(e1, A[kt][0], A[kt][1], A[kt][2], A[kt][3], t2[((2 * k3 + 1) * 4 + kt) * 32 + lane]);
+            }
+            const uint32_t h0 = pack_bf16x2(silu_f(e0[0]), silu_f(e0[1]));
+            const uint32_t h1 = pack_bf16x2(silu_f(e0[2]), silu_f(e0[3]));
+            const uint32_t h2 = pack_bf16x2(silu_f(e1[0]), silu_f(e1[1]));
+            const uint32_t h3 = pack_bf16x2(silu_f(e1[2]), silu_f(e1[3]));
+            mma_bf16_16816(d3, h0, h1, h2, h3, t3[k3 * 32 + lane]);
+        }
         // lanes with t == 0 hold (o1, o2) of rows g (d3[0..1]) and g + 8 (d3[2..3])
         const int src = 4 * (lane & 7);
         const float s0 = __shfl_sync(FULL, d3[0], src), s1 = __shfl_sync(FULL, d3[1], src);
