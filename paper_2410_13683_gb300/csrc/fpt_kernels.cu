@@ -240,8 +240,11 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
     }
 }
 
+// Register budgets: the plain stepper keeps three 512-thread blocks per SM
+// (48 warps); the learned-proposal stepper at most 384 threads per block and
+// two resident blocks, so that the network's registers still leave 24 warps.
 template <bool WEIGHTED, bool SMEM, bool MLP, bool REC>
-__global__ void __launch_bounds__(512) em_kernel(const EmParams P)
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, MLP ? 2 : 3) em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
