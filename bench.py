@@ -53,13 +53,13 @@ TAIL_P = 1e-12
 # field increment + compensated add 7, log-weight (Kahan) 5, counter + passage
 # 5, predication 2, Philox4x32-10 (40 per 4 steps) 10, uniforms + Box-Muller
 # (32 per 4 normals) 8. The learned proposal adds one network evaluation per
-# 64-step segment: 44 mma + 61 fragment loads + 128 SiLU (4 each) + 64 packs +
-# ~40 shuffles/selects per lane = ~760, i.e. 12 per step. See the design doc.
+# 128-step segment: 44 mma + 61 fragment loads + 128 SiLU (4 each) + 64 packs +
+# ~40 shuffles/selects per lane = ~760, i.e. 6 per step. See the design doc.
 INSTR_PER_STEP = 60
-INSTR_PER_STEP_MLP = 72
+INSTR_PER_STEP_MLP = 66
 # Training recipe of the learned proposal (log-variance loss towards
 # e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum).
-TRAIN = dict(rounds=240, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=64, lr0=3e-3, lr_min=3e-4)
+TRAIN = dict(rounds=300, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4)
 SM_LANES = 128
 
 
