@@ -64,7 +64,16 @@ enum {
                                 attractor pi = -V'/V                        */
     FPT_TABLE_BESSEL = 1,    /* semi-analytical Bessel-matched growing mode,
                                 Eqs. (3.10)-(3.13); needs the transition rule */
-    FPT_TABLE_USER = 2       /* caller-supplied S(phi_j), S_pi(phi_j)        */
+    FPT_TABLE_USER = 2,      /* caller-supplied S(phi_j), S_pi(phi_j)        */
+    /* N-indexed tables: the paper's production setting (Sec. 4.1), noise
+     * precomputed along the classical background as a function of the time
+     * N = n dN since the start and switched off outside the window: steps n
+     * with ceil(N_lo/dN - 1e-9) <= n <= floor(N_hi/dN + 1e-9) draw noise from
+     * the table (linear interpolation in N), all other steps are classical.
+     * For these kinds phi_lo / phi_hi carry N_lo / N_hi (required). */
+    FPT_TABLE_BESSEL_N = 3,  /* Bessel-matched noise of the mode crossing sigma a H
+                                at background time N_in + N                   */
+    FPT_TABLE_USER_N = 4     /* caller-supplied S(N_j), S_pi(N_j)            */
 };
 
 /* Bias kinds (fpt_run_desc.bias_kind). */
@@ -141,6 +150,10 @@ fpt_status fpt_model_get_info(const fpt_ctx *ctx, int32_t model, fpt_model_info 
  *   Requires the transition rule (n_in set) and 0 < sigma <= 10.
  * kind FPT_TABLE_DESITTER: S = H/2pi with H^2 = V/(3 - pi_att^2/2), S_pi = 0.
  * kind FPT_TABLE_USER: user_S / user_Spi (host, n_points doubles each, S >= 0).
+ *
+ * kind FPT_TABLE_BESSEL_N / FPT_TABLE_USER_N: as BESSEL / USER on the grid
+ *   N_j = N_lo + j h of times since the start (see the enum); learned-proposal
+ *   runs need a phi-indexed table.
  *
  * out_S, out_Spi: optional host buffers of n_points doubles receiving the FP64
  * table. Blocks the calling thread until the upload finished.

@@ -105,9 +105,12 @@ typedef struct {
 
 typedef struct {
     int64_t n_points;    /* M >= 2 */
-    double phi_lo, h;    /* grid phi_j = phi_lo + j h */
-    const double *S;     /* S_phiphi(phi_j)                      */
-    const double *T;     /* S_piphi(phi_j) = tan(theta_n) S(phi_j) */
+    double phi_lo, h;    /* grid phi_j = phi_lo + j h (N-indexed: N_j = phi_lo + j h) */
+    const double *S;     /* S_phiphi at the grid points              */
+    const double *T;     /* S_piphi = tan(theta_n) S at the grid points */
+    int32_t n_indexed;   /* 1: indexed by the time N = n dN since the start, with
+                            zero noise outside [N_0, N_{M-1}] (the noise window) */
+    int32_t pad;
 } oracle_table;
 
 typedef struct {
@@ -132,7 +135,10 @@ static double dlnV(const oracle_model *m, double phi)
     return a / (1.0 + a * d);
 }
 
-/* Linear interpolation of the noise table, end values held outside. */
+/* Linear interpolation of the noise table. phi-indexed tables hold their end
+ * values outside the grid; N-indexed tables (the paper's production setting,
+ * Sec. 4.1: noise precomputed along the classical background in global time
+ * and switched off after a window) give zero noise outside it. */
 static void table_lookup(const oracle_table *t, double phi, double *S, double *T)
 {
     double M1 = (double)(t->n_points - 1);
@@ -234,6 +240,13 @@ static void one_trajectory(const oracle_model *m, const oracle_table *tab,
 {
     const double dN = m->dN, sdN = sqrt(m->dN);
     double phi = m->phi_in, pi = m->pi_in, lw = 0.0, xm = INFINITY;
+    /* N-indexed tables: the window is the integer step range whose times n dN
+     * lie in [N_0, N_{M-1}] (with a 1e-9 allowance for the division) */
+    int64_t win_lo = 0, win_hi = -1;
+    if (tab->n_indexed) {
+        win_lo = (int64_t)ceil(tab->phi_lo / dN - 1e-9);
+        win_hi = (int64_t)floor((tab->phi_lo + tab->h * (double)(tab->n_points - 1)) / dN + 1e-9);
+    }
     double z[4];
     double alpha = (b->kind == 1) ? b->A : 0.0;
     int64_t n = 0, ns = 0;
@@ -242,8 +255,14 @@ static void one_trajectory(const oracle_model *m, const oracle_table *tab,
         if ((n & 3) == 0)
             oracle_normals4(seed, run_id, traj, (uint32_t)(n >> 2), z);
         double xi = z[n & 3];
-        double S, T;
-        table_lookup(tab, phi, &S, &T);
+        double S = 0.0, T = 0.0;
+        int noisy = 1;
+        if (!tab->n_indexed)
+            table_lookup(tab, phi, &S, &T);
+        else if (n >= win_lo && n <= win_hi)   /* step inside the noise window */
+            table_lookup(tab, (double)n * dN, &S, &T);
+        else
+            noisy = 0;                         /* classical step: no noise, no bias, no weight */
         if (b->kind == 2 && (n % b->segment) == 0) {
             double t = (S != 0.0) ? T / S : 0.0;
             alpha = mlp_alpha(b, m, phi, pi, n, t);
@@ -261,10 +280,11 @@ static void one_trajectory(const oracle_model *m, const oracle_table *tab,
         }
         if (b->kind == 2 && seg && ns - 1 < seg->cap)
             seg->sum_xi[ns - 1] += xi;
+        const double a = noisy ? alpha : 0.0;
         double drift_pi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi));
-        double phi_new = phi + pi * dN + alpha * S * dN + S * xi * sdN;
-        double pi_new = pi + drift_pi * dN + alpha * T * dN + T * xi * sdN;
-        lw -= alpha * (0.5 * alpha * dN + xi * sdN);
+        double phi_new = phi + pi * dN + a * S * dN + S * xi * sdN;
+        double pi_new = pi + drift_pi * dN + a * T * dN + T * xi * sdN;
+        lw -= a * (0.5 * a * dN + xi * sdN);
         phi = phi_new;
         pi = pi_new;
         ++n;

@@ -37,7 +37,8 @@ class _Model(C.Structure):
 
 class _Table(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("phi_lo", C.c_double), ("h", C.c_double),
-                ("S", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double))]
+                ("S", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double)),
+                ("n_indexed", C.c_int32), ("pad", C.c_int32)]
 
 
 class _Bias(C.Structure):
@@ -164,7 +165,8 @@ def run(m, resolved, table, seed: int, run_id: int, n: int, traj0: int = 0,
     """FP64 trajectories traj0 .. traj0+n-1 of one run."""
     S = np.ascontiguousarray(table.S, dtype=np.float64)
     T = np.ascontiguousarray(table.T, dtype=np.float64)
-    tab = _Table(n_points=len(S), phi_lo=table.phi_lo, h=table.h, S=_dp(S), T=_dp(T))
+    tab = _Table(n_points=len(S), phi_lo=table.phi_lo, h=table.h, S=_dp(S), T=_dp(T),
+                 n_indexed=int(getattr(table, "n_indexed", False)), pad=0)
     ms = model_struct(m, resolved.phi_in, resolved.pi_in, resolved.phi_end)
     b = bias_struct(A, mlp)
     out = dict(nsteps=np.zeros(n, np.int64), logw=np.zeros(n), status=np.zeros(n, np.uint8),
@@ -185,7 +187,8 @@ def run_segments(m, resolved, table, mlp: MLPBias, seed: int, run_id: int, traj:
     """One learned-bias trajectory with its per-segment records."""
     S = np.ascontiguousarray(table.S, dtype=np.float64)
     T = np.ascontiguousarray(table.T, dtype=np.float64)
-    tab = _Table(n_points=len(S), phi_lo=table.phi_lo, h=table.h, S=_dp(S), T=_dp(T))
+    tab = _Table(n_points=len(S), phi_lo=table.phi_lo, h=table.h, S=_dp(S), T=_dp(T),
+                 n_indexed=int(getattr(table, "n_indexed", False)), pad=0)
     ms = model_struct(m, resolved.phi_in, resolved.pi_in, resolved.phi_end)
     b = mlp.struct()
     n_seg = C.c_int64(0)

@@ -292,10 +292,11 @@ def noise_at_phi(m, res: Resolved, phi: float, sigma: float) -> ModeNoise:
 
 @dataclass
 class NoiseTable:
-    phi_lo: float
+    phi_lo: float              # first grid coordinate (phi, or N for n_indexed)
     h: float
     S: np.ndarray
     T: np.ndarray
+    n_indexed: bool = False    # indexed by time since the start; zero noise outside
 
     @property
     def n_points(self):
@@ -349,6 +350,47 @@ def bessel_table(m, res: Resolved, n_points: int, sigma: float, phi_lo=None, phi
     for j, (s, t) in zip(idx, out):
         S[j], T[j] = s, t
     return NoiseTable(lo, h, S, T)
+
+
+def noise_at_time(m, res: Resolved, N_since_start: float, sigma: float) -> ModeNoise:
+    """Bessel-matched noise of the mode that crosses sigma a H at background
+    time N_in + N_since_start (the paper's global-time indexing, Sec. 4.1)."""
+    bg = res.bg
+    N_s = res.N_in + N_since_start
+    ph, pi, br = bg.state(N_s)
+    return noise_at_phi(m, res, ph, sigma)
+
+
+def _bessel_time_worker(args):
+    m, res, N, sigma = args
+    r = noise_at_time(m, res, N, sigma)
+    return r.S, r.T
+
+
+def bessel_table_N(m, res: Resolved, n_points: int, sigma: float, N_lo: float, N_hi: float,
+                   indices=None, processes: int = 0) -> NoiseTable:
+    """Noise along the classical background on a uniform grid of the time
+    since the start, N_j = N_lo + j h; zero outside [N_lo, N_hi] (window)."""
+    Ns, h = grid(n_points, N_lo, N_hi)
+    idx = range(n_points) if indices is None else list(indices)
+    S = np.full(n_points, np.nan)
+    T = np.full(n_points, np.nan)
+    jobs = [(m, res, float(Ns[j]), sigma) for j in idx]
+    if processes and processes > 1 and len(jobs) > 8:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            out = pool.map(_bessel_time_worker, jobs, chunksize=max(1, len(jobs) // (4 * processes)))
+    else:
+        out = [_bessel_time_worker(j) for j in jobs]
+    for j, (sv, tv) in zip(idx, out):
+        S[j], T[j] = sv, tv
+    return NoiseTable(N_lo, h, S, T, n_indexed=True)
+
+
+def user_table_N(S, T, N_lo, N_hi) -> NoiseTable:
+    S = np.asarray(S, float)
+    T = np.asarray(T, float)
+    return NoiseTable(N_lo, (N_hi - N_lo) / (len(S) - 1), S, T, n_indexed=True)
 
 
 def user_table(S, T, phi_lo, phi_hi) -> NoiseTable:

@@ -30,6 +30,7 @@ std::string g_init_err = "no error";
 
 struct TableHost {
     bool ready = false;
+    bool n_indexed = false;    // grid in time since the start (noise window)
     int M = 0;
     double lo = 0, h = 0;
     std::vector<double> S, T;
@@ -225,8 +226,14 @@ fpt_status fpt_resolve_model(const fpt_model *model, fpt_model_info *out)
 static fpt_status table_args(int kind, int n_points, double sigma, double phi_lo, double phi_hi,
                              const double *uS, const double *uT, std::string &msg)
 {
-    if (kind != FPT_TABLE_DESITTER && kind != FPT_TABLE_BESSEL && kind != FPT_TABLE_USER) {
+    if (kind != FPT_TABLE_DESITTER && kind != FPT_TABLE_BESSEL && kind != FPT_TABLE_USER &&
+        kind != FPT_TABLE_BESSEL_N && kind != FPT_TABLE_USER_N) {
         msg = "unknown table kind";
+        return FPT_E_INVALID;
+    }
+    if ((kind == FPT_TABLE_BESSEL_N || kind == FPT_TABLE_USER_N) &&
+        (std::isnan(phi_lo) || !(phi_lo >= 0.0))) {
+        msg = "N-indexed tables need 0 <= N_lo < N_hi";
         return FPT_E_INVALID;
     }
     if (n_points < 2 || n_points > kMaxTablePoints) { msg = "n_points out of [2, 8192]"; return FPT_E_INVALID; }
@@ -235,8 +242,11 @@ static fpt_status table_args(int kind, int n_points, double sigma, double phi_lo
         msg = "need finite phi_lo < phi_hi";
         return FPT_E_INVALID;
     }
-    if (kind == FPT_TABLE_BESSEL && !(sigma > 0 && sigma <= 10)) { msg = "sigma out of (0, 10]"; return FPT_E_INVALID; }
-    if (kind == FPT_TABLE_USER) {
+    if ((kind == FPT_TABLE_BESSEL || kind == FPT_TABLE_BESSEL_N) && !(sigma > 0 && sigma <= 10)) {
+        msg = "sigma out of (0, 10]";
+        return FPT_E_INVALID;
+    }
+    if (kind == FPT_TABLE_USER || kind == FPT_TABLE_USER_N) {
         if (!uS || !uT) { msg = "USER tables need user_S and user_Spi"; return FPT_E_INVALID; }
         for (int j = 0; j < n_points; ++j)
             if (!(uS[j] >= 0) || !std::isfinite(uS[j]) || !std::isfinite(uT[j])) {
@@ -252,7 +262,7 @@ static fpt_status build_host_table(const fpt_model &m, const fpt_model_info &inf
                                    const double *uS, const double *uT, TableHost &t, std::string &msg)
 {
     try {
-        if (kind == FPT_TABLE_USER) {
+        if (kind == FPT_TABLE_USER || kind == FPT_TABLE_USER_N) {
             double lo = std::isnan(phi_lo) ? info.phi_end : phi_lo;
             double hi = std::isnan(phi_hi) ? info.phi_in : phi_hi;
             if (!(hi > lo)) { msg = "need phi_hi > phi_lo"; return FPT_E_INVALID; }
@@ -269,6 +279,7 @@ static fpt_status build_host_table(const fpt_model &m, const fpt_model_info &inf
     }
     t.M = n_points;
     t.ready = true;
+    t.n_indexed = (kind == FPT_TABLE_BESSEL_N || kind == FPT_TABLE_USER_N);
     return FPT_OK;
 }
 
@@ -277,7 +288,8 @@ fpt_status fpt_table_build(const fpt_model *model, int32_t kind, int32_t n_point
 {
     if (!model || !out_S || !out_Spi) return fail(nullptr, FPT_E_INVALID, "null argument");
     std::string msg;
-    if (kind == FPT_TABLE_USER) return fail(nullptr, FPT_E_INVALID, "USER tables are not built");
+    if (kind == FPT_TABLE_USER || kind == FPT_TABLE_USER_N)
+        return fail(nullptr, FPT_E_INVALID, "USER tables are not built");
     fpt_status s = table_args(kind, n_points, sigma, phi_lo, phi_hi, nullptr, nullptr, msg);
     if (s != FPT_OK) return fail(nullptr, s, msg);
     fpt_model_info info;
@@ -389,8 +401,19 @@ static fpt_status upload_tables(fpt_ctx *ctx)
         d.table_offset = ctx->table_offset[i];
         if (t.ready) {
             d.M = t.M;
-            d.u_scale = (float)(1.0 / t.h);
-            d.u_shift = (float)((inf.phi_end - t.lo) / t.h);
+            if (t.n_indexed) {
+                // u = (n dN - N_lo)/h; window of steps as in the oracle's definition
+                d.nidx = 1;
+                d.u_scale = (float)(m.dN / t.h);
+                d.u_shift = (float)(-t.lo / t.h);
+                const double lo_s = std::ceil(t.lo / m.dN - 1e-9);
+                const double hi_s = std::floor((t.lo + t.h * (t.M - 1)) / m.dN + 1e-9);
+                d.win_lo = (int32_t)std::max(0.0, std::min(lo_s, 2147483647.0));
+                d.win_hi = (int32_t)std::max(-1.0, std::min(hi_s, 2147483647.0));
+            } else {
+                d.u_scale = (float)(1.0 / t.h);
+                d.u_shift = (float)((inf.phi_end - t.lo) / t.h);
+            }
             const double sq = std::sqrt(m.dN);
             for (int j = 0; j < t.M; ++j) {
                 const int k = std::min(j + 1, t.M - 1);
@@ -507,6 +530,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     std::set<int> used_models;
     long long total = 0;
     bool weighted = false;
+    bool nidx = false;
     int mlp_run = -1;
     for (int r = 0; r < n_runs; ++r) {
         const fpt_run_desc &d = runs[r];
@@ -539,6 +563,11 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
         if (d.seed != runs[0].seed) return fail(ctx, FPT_E_INVALID, "all runs of one call must share the seed");
         if (d.n_traj > 0) used_models.insert(d.model);
         if ((d.bias_kind == FPT_BIAS_CONST && d.A != 0.0) || d.bias_kind == FPT_BIAS_MLP) weighted = true;
+        if (d.n_traj > 0 && ctx->tables[d.model].n_indexed) {
+            if (d.bias_kind == FPT_BIAS_MLP)
+                return fail(ctx, FPT_E_INVALID, "learned-proposal runs need a phi-indexed noise table");
+            nidx = true;
+        }
         total += d.n_traj;
     }
     if (total > (1LL << 32)) return fail(ctx, FPT_E_INVALID, "more than 2^32 trajectories in one call");
@@ -581,7 +610,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const bool smem = used_models.size() == 1;
     const int smem_model = smem ? *used_models.begin() : 0;
     const bool mlp = mlp_run >= 0;
-    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode};
+    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp};
     const size_t smem_bytes = (smem ? sizeof(float4) * ctx->tables[smem_model].M : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
     // the learned-proposal stepper is compiled for at most kMlpMaxBlock threads
@@ -622,7 +651,8 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     if (total > 0) {
         if (graph) {
             GraphKey key{weighted, smem, grid, block, smem_bytes, p.groups_per_check, n_runs,
-                         smem ? smem_model : -1, total, (mlp ? 1 : 0) + (var.rec ? 2 : 0) + 4 * p.mlp_run};
+                         smem ? smem_model : -1, total,
+                         (mlp ? 1 : 0) + (var.rec ? 2 : 0) + (var.nidx ? 4 : 0) + 8 * p.mlp_run};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 cudaGraph_t g;

@@ -45,7 +45,8 @@ struct ModelDev {
     int32_t M;                 // table points
     int32_t max_steps;
     int32_t table_offset;      // first float4 entry of this model's table
-    int32_t pad;
+    int32_t nidx;              // 1: table indexed by the step count (noise window)
+    int32_t win_lo, win_hi;    // noise window [win_lo, win_hi] in steps (nidx)
 };
 
 // One run of a launch (FP32 constants; 64-bit unit bookkeeping).
@@ -117,7 +118,7 @@ enum {
 // Stepper variants: weighted (any bias), table in shared memory, learned
 // proposal, segment records.
 struct EmVariant {
-    bool weighted, smem, mlp, rec;
+    bool weighted, smem, mlp, rec, nidx;
 };
 
 // Host wrappers implemented in fpt_kernels.cu.

@@ -106,6 +106,8 @@ struct Lane {                // per-thread trajectory state and its constants
     float u_scale, u_shift, u_max;
     int tbase;
     bool mlp;
+    bool nidx;               // noise table indexed by the step count
+    int win_lo, win_hi;      // noise window in steps (nidx)
     long long unit;
 };
 
@@ -143,6 +145,9 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.u_shift = m.u_shift;
     L.u_max = (float)(m.M - 1);
     L.tbase = m.table_offset;
+    L.nidx = m.nidx != 0;
+    L.win_lo = m.win_lo;
+    L.win_hi = m.win_hi;
     L.nmax = m.max_steps;
     L.x = m.x_in;
     L.x_c = 0.0f;
@@ -157,11 +162,13 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
 // comes from adding 1.5 2^23 (round to nearest in the mantissa), so index and
 // weight f = u - k in [0, 1] need no float/int conversion. k = M - 1 happens
 // only at u = M - 1 with f = 0, and entry M - 1 carries zero slopes.
-template <bool SMEM>
+template <bool SMEM, bool NIDX = false>
 __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restrict__ tab, float &f)
 {
     const float kMagic = 12582912.0f;                        // 1.5 * 2^23
-    float u = fmaf(L.x, L.u_scale, L.u_shift);
+    // N-indexed tables: coordinate from the exact step count (n < 2^24 is exact in FP32)
+    const float coord = (NIDX && L.nidx) ? __int2float_rn(L.n) : L.x;
+    float u = fmaf(coord, L.u_scale, L.u_shift);
     u = fminf(fmaxf(u, 0.0f), L.u_max);
     const float t = (u - 0.5f) + kMagic;
     const int i = __float_as_int(t) - 0x4b400000;
@@ -174,14 +181,22 @@ __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restri
 // compensated field pair: a plain FP32 field would add the same drift
 // increment to a value on its own grid every step, a rounding error with a
 // fixed sign. Returns true when the trajectory has finished (passage or cap).
-template <bool WEIGHTED, bool SMEM>
+template <bool WEIGHTED, bool SMEM, bool NIDX = false>
 __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab)
 {
-    // noise table: linear interpolation in x, end values held outside
+    // noise table: linear interpolation in x (or in time), end values held outside
     float f;
-    const float4 e = table_at<SMEM>(L, tab, f);
-    const float S = fmaf(f, e.y, e.x);         // S_phiphi sqrt(dN)
-    const float T = fmaf(f, e.w, e.z);         // tan(theta_n) S_phiphi sqrt(dN)
+    const float4 e = table_at<SMEM, NIDX>(L, tab, f);
+    float S = fmaf(f, e.y, e.x);               // S_phiphi sqrt(dN)
+    float T = fmaf(f, e.w, e.z);               // tan(theta_n) S_phiphi sqrt(dN)
+    float cb = L.cb, half_cb2 = L.half_cb2;
+    if (NIDX && L.nidx && (L.n < L.win_lo || L.n > L.win_hi)) {
+        // outside the noise window the step is classical: no noise, no bias, no weight
+        S = 0.0f;
+        T = 0.0f;
+        cb = 0.0f;
+        half_cb2 = 0.0f;
+    }
     // drift: V'/V of the piecewise-linear (or exponential) potential
     const float d = L.x - L.x_star;
     const bool up = d >= 0.0f;
@@ -189,10 +204,10 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     const float b = up ? L.b_plus : L.b_minus;
     const float vpv = __fdividef(a, fmaf(b, d, 1.0f));
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
-    const float zb = z + L.cb;                           // xi + alpha sqrt(dN)
+    const float zb = z + cb;                             // xi + alpha sqrt(dN)
     const float dx = fmaf(S, zb, L.p * L.dN);           // (pi + alpha S) dN + S xi sqrt(dN)
     const float pn = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
-    if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z, L.half_cb2));
+    if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(cb, z, half_cb2));
     kahan_add(L.x, L.x_c, dx);
     L.p = pn;
     ++L.n;
@@ -243,8 +258,8 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
 // Register budgets: the plain stepper keeps three 512-thread blocks per SM
 // (48 warps); the learned-proposal stepper at most 384 threads per block and
 // two resident blocks, so that the network's registers still leave 24 warps.
-template <bool WEIGHTED, bool SMEM, bool MLP, bool REC>
-__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, MLP ? 2 : 3) em_kernel(const EmParams P)
+template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX>
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 3) em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
@@ -300,7 +315,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, MLP ? 2 : 3) em_kern
         const long long unit = (long long)(base + lane);
         active = unit < P.total_units;
         if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
-        else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false;
+        else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false, L.nidx = false;
     }
 
     for (;;) {
@@ -317,7 +332,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, MLP ? 2 : 3) em_kern
             for (int s = 0; s < 4; ++s)
                 if (active && !done) {
                     if (REC) sg.sum_xi += z[s];
-                    done = em_step<WEIGHTED, SMEM>(L, z[s], tab);
+                    done = em_step<WEIGHTED, SMEM, NIDX>(L, z[s], tab);
                 }
         }
 
@@ -382,10 +397,20 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, MLP ? 2 : 3) em_kern
 
 static const void *em_fn(EmVariant v)
 {
-    if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true> : (const void *)em_kernel<true, false, true, true>;
-    if (v.mlp) return v.smem ? (const void *)em_kernel<true, true, true, false> : (const void *)em_kernel<true, false, true, false>;
-    if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false> : (const void *)em_kernel<true, false, false, false>;
-    return v.smem ? (const void *)em_kernel<false, true, false, false> : (const void *)em_kernel<false, false, false, false>;
+    if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true, false>
+                             : (const void *)em_kernel<true, false, true, true, false>;
+    if (v.mlp) return v.smem ? (const void *)em_kernel<true, true, true, false, false>
+                             : (const void *)em_kernel<true, false, true, false, false>;
+    if (v.nidx) {
+        if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, true>
+                                      : (const void *)em_kernel<true, false, false, false, true>;
+        return v.smem ? (const void *)em_kernel<false, true, false, false, true>
+                      : (const void *)em_kernel<false, false, false, false, true>;
+    }
+    if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, false>
+                                  : (const void *)em_kernel<true, false, false, false, false>;
+    return v.smem ? (const void *)em_kernel<false, true, false, false, false>
+                  : (const void *)em_kernel<false, false, false, false, false>;
 }
 
 // Opt in to the dynamic shared memory the table (and proposal) need, outside

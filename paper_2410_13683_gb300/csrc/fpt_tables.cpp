@@ -375,12 +375,13 @@ static double nu_squared(const fpt_model &m, double phi, double pi, int branch)
     return 2.25 - eps1 - 0.5 * eps1 * eps2 * eps2 / (3.0 - eps1) + (eps1 - 3.0) * (d2lnV_term(m) - v1 * v1);
 }
 
-// Bessel-matched noise (S, S_pi) at field value phi.
-static void bessel_noise(const fpt_model &m, const Resolved &r, double phi, double sigma,
-                         double &S, double &Spi)
+// Bessel-matched noise (S, S_pi) of the mode that crosses sigma a H at
+// background time Ns.
+static void bessel_noise_at_N(const fpt_model &m, const Resolved &r, double Ns, double sigma,
+                              double &S, double &Spi)
 {
     const Background &bg = r.bg;
-    double Ns = N_of_phi(bg, phi, bg.N_T, bg.N_max());
+    if (!(Ns >= bg.N_T) || !(Ns <= bg.N_max())) throw std::runtime_error("table time outside the post-transition background");
     double ph, pi;
     int br;
     bg.state(Ns, ph, pi, br);
@@ -405,6 +406,13 @@ static void bessel_noise(const fpt_model &m, const Resolved &r, double phi, doub
     S = (H / (2.0 * kPi)) * (2.0 * std::abs(B) / std::sqrt(kPi)) *
         (std::tgamma(nu) / std::tgamma(1.5)) * std::pow(0.5 * sigma, 1.5 - nu);
     Spi = (nu - 1.5) * S;
+}
+
+// Bessel-matched noise at field value phi (post-transition background).
+static void bessel_noise(const fpt_model &m, const Resolved &r, double phi, double sigma,
+                         double &S, double &Spi)
+{
+    bessel_noise_at_N(m, r, N_of_phi(r.bg, phi, r.bg.N_T, r.bg.N_max()), sigma, S, Spi);
 }
 
 // ---------------------------------------------------------------------------
@@ -445,6 +453,9 @@ void build_table(const fpt_model &m, int kind, int n_points, double sigma, doubl
                  double &lo_out, double &h_out)
 {
     Resolved r = resolve_full(m);
+    const bool by_time = kind == FPT_TABLE_BESSEL_N;
+    if (by_time && (std::isnan(phi_lo) || std::isnan(phi_hi)))
+        throw std::runtime_error("N-indexed tables need N_lo and N_hi");
     double lo = std::isnan(phi_lo) ? r.info.phi_end : phi_lo;
     double hi = std::isnan(phi_hi) ? r.info.phi_in : phi_hi;
     if (!(hi > lo)) throw std::runtime_error("need phi_hi > phi_lo");
@@ -461,7 +472,7 @@ void build_table(const fpt_model &m, int kind, int n_points, double sigma, doubl
         }
         return;
     }
-    if (kind != FPT_TABLE_BESSEL) throw std::runtime_error("unknown table kind");
+    if (kind != FPT_TABLE_BESSEL && kind != FPT_TABLE_BESSEL_N) throw std::runtime_error("unknown table kind");
     if (!r.has_bg) throw std::runtime_error("Bessel tables need the transition rule (n_in set)");
     if (!(sigma > 0 && sigma <= 10)) throw std::runtime_error("sigma out of (0, 10]");
     unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
@@ -475,7 +486,8 @@ void build_table(const fpt_model &m, int kind, int n_points, double sigma, doubl
                 int j = next.fetch_add(1);
                 if (j >= n_points || failed.load()) break;
                 try {
-                    bessel_noise(m, r, lo + h * j, sigma, S[j], Spi[j]);
+                    if (by_time) bessel_noise_at_N(m, r, r.N_in + lo + h * j, sigma, S[j], Spi[j]);
+                    else bessel_noise(m, r, lo + h * j, sigma, S[j], Spi[j]);
                 } catch (const std::exception &e) {
                     if (!failed.exchange(true)) err = e.what();
                 }

@@ -24,7 +24,7 @@ NAN = float("nan")
 FPT_OK, FPT_E_INVALID, FPT_E_CUDA, FPT_E_NOMEM, FPT_E_TIMEOUT, FPT_E_STATE = 0, 1, 2, 3, 4, 5
 FPT_W_CAPPED = 100
 FPT_POT_PWLINEAR, FPT_POT_EXP = 0, 1
-FPT_TABLE_DESITTER, FPT_TABLE_BESSEL, FPT_TABLE_USER = 0, 1, 2
+FPT_TABLE_DESITTER, FPT_TABLE_BESSEL, FPT_TABLE_USER, FPT_TABLE_BESSEL_N, FPT_TABLE_USER_N = 0, 1, 2, 3, 4
 FPT_BIAS_NONE, FPT_BIAS_CONST, FPT_BIAS_MLP = 0, 1, 2
 FPT_TRAJ_PASSED, FPT_TRAJ_CAPPED, FPT_TRAJ_ABORTED = 0, 1, 2
 FPT_MLP_LOG_X = 1
@@ -281,7 +281,7 @@ def fpt_noise_table(ctx: Context, model: int, kind: int, n_points: int, sigma: f
     S = np.zeros(n_points)
     T = np.zeros(n_points)
     uS = uT = None
-    if kind == FPT_TABLE_USER:
+    if kind in (FPT_TABLE_USER, FPT_TABLE_USER_N):
         uS = np.ascontiguousarray(user_S, dtype=np.float64)
         uT = np.ascontiguousarray(user_Spi, dtype=np.float64)
         if uS.shape != (n_points,) or uT.shape != (n_points,):

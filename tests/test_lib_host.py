@@ -126,3 +126,24 @@ def test_context_needs_a_gpu_or_fails_loudly():
     with pytest.raises(fpt.FptError) as e:
         fpt.fpt_init_model([W.LINEAR.model])
     assert e.value.status == fpt.FPT_E_CUDA
+
+
+def test_time_indexed_bessel_table_matches_oracle():
+    """Noise along the classical background in global time (the paper's
+    production setting): library vs oracle at sampled grid times."""
+    m = W.USR_MODEL
+    r = T.resolve(m)
+    Nw = m.n_end - m.n_in
+    S, Sp = fpt.fpt_table_build(m, fpt.FPT_TABLE_BESSEL_N, 512, 1.0, 0.0, Nw)
+    idx = [0, 1, 100, 256, 510, 511]
+    tab = T.bessel_table_N(m, r, 512, 1.0, 0.0, Nw, indices=idx)
+    np.testing.assert_allclose(S[idx], tab.S[idx], rtol=1e-8)
+    # the time-indexed table at time N equals the phi-indexed one at phi_bg(N_in + N)
+    ph, _, _ = r.bg.state(r.N_in + Nw * 256 / 511)
+    S_phi, _ = fpt.fpt_table_build(m, fpt.FPT_TABLE_BESSEL, 2, 1.0, ph, ph + 1e-9)
+    assert S[256] == pytest.approx(S_phi[0], rel=1e-7)
+
+
+def test_time_indexed_table_needs_a_window():
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_table_build(W.USR_MODEL, fpt.FPT_TABLE_BESSEL_N, 64, 1.0)

@@ -140,3 +140,57 @@ def test_near_tie_diagnostics():
     m, res, tab, tr = _bm(n=256)
     assert np.all(tr.phi_final <= 0.0)
     assert np.all((tr.xmin_pre > 0) | (tr.nsteps == 1))
+
+
+def test_noise_window_random_walk_identity():
+    """N-indexed noise with a window (noise on for N in [0, N_w], then the
+    classical completion): on the exponential model every path satisfies
+    phi_n = phi_0 - mu n dN + s sqrt(dN) sum_{i < n, i dN <= N_w} xi_i exactly."""
+    m = W.BM.model
+    res = T.resolve(m)
+    Nw = 2.0
+    tab = T.user_table_N(np.full(16, W.BM_S), np.zeros(16), 0.0, Nw)
+    tr = S.run(m, res, tab, seed=9, run_id=0, n=200)
+    sdN = math.sqrt(m.dN)
+    late = 0
+    for j in range(200):
+        n = int(tr.nsteps[j])
+        xi = np.concatenate([S.normals4(9, 0, j, b) for b in range((n + 3) // 4)])[:n]
+        on = np.arange(n) <= math.floor(Nw / m.dN + 1e-9)     # integer window of steps
+        phi = m.phi_in - n * W.BM_MU * m.dN + W.BM_S * sdN * xi[on].sum()
+        assert abs(tr.phi_final[j] - phi) < 1e-12
+        late += n * m.dN > Nw
+    assert late > 150          # most paths finish after the window, classically
+    # after the window the remaining field falls by exactly mu dN per step
+    full = T.user_table(np.full(16, W.BM_S), np.zeros(16), -0.1, 0.2)
+    tr_full = S.run(m, res, full, seed=9, run_id=0, n=200)
+    assert not np.array_equal(tr.nsteps, tr_full.nsteps)
+
+
+def test_noise_window_covering_the_run_equals_phi_indexed():
+    m = W.BM.model
+    res = T.resolve(m)
+    a = S.run(m, res, T.user_table_N(np.full(16, W.BM_S), np.zeros(16), 0.0, 100.0), seed=3, run_id=0, n=256)
+    b = S.run(m, res, T.user_table(np.full(16, W.BM_S), np.zeros(16), -0.1, 0.2), seed=3, run_id=0, n=256)
+    assert np.array_equal(a.nsteps, b.nsteps) and np.array_equal(a.logw, b.logw)
+
+
+def test_noise_window_weight_acts_only_on_noisy_steps():
+    """Outside the window the step is classical: no noise, no bias and no
+    weight change, so ln w = -sum over window steps of A (A dN/2 + xi sqrt(dN))."""
+    m = W.BM.model
+    res = T.resolve(m)
+    A, Nw = 0.8, 1.5
+    tab = T.user_table_N(np.full(16, W.BM_S), np.zeros(16), 0.25, Nw)
+    tr = S.run(m, res, tab, seed=10, run_id=0, n=100, A=A)
+    sdN = math.sqrt(m.dN)
+    lo, hi = math.ceil(0.25 / m.dN - 1e-9), math.floor(Nw / m.dN + 1e-9)
+    for j in range(100):
+        n = int(tr.nsteps[j])
+        xi = np.concatenate([S.normals4(10, 0, j, b) for b in range((n + 3) // 4)])[:n]
+        idx = np.arange(n)
+        win = (idx >= lo) & (idx <= hi)
+        lw = -np.sum(A * (0.5 * A * m.dN + xi[win] * sdN))
+        assert abs(tr.logw[j] - lw) < 1e-9 * max(1.0, abs(lw))
+        phi = m.phi_in - n * W.BM_MU * m.dN + np.sum(W.BM_S * (A * m.dN + sdN * xi[win]))
+        assert abs(tr.phi_final[j] - phi) < 1e-12
