@@ -32,7 +32,7 @@ def gpu_run(ctx, runs, n_list, stream=None):
     return st, outs
 
 
-def compare(g, o, x_in, label=""):
+def compare(g, o, x_in, label="", max_mismatch=MAX_MISMATCH, max_step_diff=None):
     """Per-trajectory parity of GPU outputs ``g`` with oracle trajectories ``o``.
 
     Step counts must be equal except for near-ties: trajectories whose FP64
@@ -49,7 +49,10 @@ def compare(g, o, x_in, label=""):
     mism = g["nsteps"].astype(np.int64) != o.nsteps
     bad = mism & ~near
     assert not bad.any(), f"{label}: {bad.sum()} non-near-tie step mismatches, e.g. {np.flatnonzero(bad)[:5]}"
-    assert mism.mean() <= MAX_MISMATCH, f"{label}: mismatch fraction {mism.mean():.4f}"
+    assert mism.mean() <= max_mismatch, f"{label}: mismatch fraction {mism.mean():.4f}"
+    if max_step_diff is not None and mism.any():
+        d = np.abs(g["nsteps"].astype(np.int64) - o.nsteps)[mism]
+        assert d.max() <= max_step_diff, f"{label}: near-tie step difference {d.max()}"
     ok = ~mism
     assert np.array_equal(g["status"][ok], o.status[ok]), label
     np.testing.assert_array_equal(g["N"][ok], o.nsteps[ok] * o.dN)

@@ -54,7 +54,16 @@ def test_window_usr_parity(torch):
         assert st == fpt.FPT_OK
     tab = OT.bessel_table_N(m, res, n_pts, 1.0, 0.0, Nw, processes=8)
     np.testing.assert_allclose(S, tab.S, rtol=1e-8)
+    # After the window the completion is classical at the late slow-roll
+    # velocity pi dN ~ 1e-9 per step, below tau = 1e-5 x_in = 2.5e-9: every
+    # post-window passage is a near-tie, and a field difference of ~1e-10
+    # (FP32 state vs FP64) moves it by at most one step. So each mismatch must
+    # be a near-tie and at most one step off; their fraction is bounded only
+    # loosely (25%): a window error would move the field by S xi ~ 4e-8 >> tau
+    # and fail as a non-near-tie.
     for r, A in enumerate([0.0, 1.0]):
         o = OS.run(m, res, tab, seed=71, run_id=r, n=n, A=A)
         o.phi_end_value = res.phi_end
-        compare(g[r], o, res.phi_in - res.phi_end, f"usr window A={A}")
+        mism, near = compare(g[r], o, res.phi_in - res.phi_end, f"usr window A={A}",
+                             max_mismatch=0.25, max_step_diff=1)
+        print(f"usr window A={A}: mismatch {mism:.4%}, near-ties {near:.4%}")
