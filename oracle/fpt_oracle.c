@@ -301,6 +301,106 @@ static void one_trajectory(const oracle_model *m, const oracle_table *tab,
     if (seg) *seg->n_seg = ns < seg->cap ? ns : seg->cap;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Full-rank (2-D) noise: Euler-Maruyama of Eq. (2.24) with the symmetric     */
+/* square root S of the covariance Xi of Eq. (3.9); two normals per step      */
+/* (step i uses normals 2(i & 1) and 2(i & 1) + 1 of Philox block i >> 1).    */
+/* The bias is written in standardised form, B = S beta, so that Eq. (4.5)    */
+/* gives dA = (S beta dN/2 + S xi sqrt(dN))^T Xi^-1 S beta                    */
+/*          = beta . (beta dN/2 + xi sqrt(dN))   (S^T Xi^-1 S = 1).           */
+/* beta = (A, A2) for a constant bias; for the learned proposal               */
+/* beta = (clamp(o1), clamp(o2)), the two MLP outputs, each clamped to        */
+/* +-alpha_max and held for `segment` steps.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_points;
+    double phi_lo, h;
+    const double *Spp, *Spq, *Sqq;   /* S_phiphi, S_phipi = S_piphi, S_pipi */
+} oracle_table2;
+
+static void table2_lookup(const oracle_table2 *t, double phi, double *a, double *b, double *c)
+{
+    double M1 = (double)(t->n_points - 1);
+    double u = (phi - t->phi_lo) / t->h;
+    if (u < 0.0) u = 0.0;
+    if (u > M1) u = M1;
+    int64_t i = (int64_t)floor(u);
+    if (i > t->n_points - 2) i = t->n_points - 2;
+    double f = u - (double)i;
+    *a = t->Spp[i] + f * (t->Spp[i + 1] - t->Spp[i]);
+    *b = t->Spq[i] + f * (t->Spq[i + 1] - t->Spq[i]);
+    *c = t->Sqq[i] + f * (t->Sqq[i + 1] - t->Sqq[i]);
+}
+
+static double clampd(double v, double lim)
+{
+    return v > lim ? lim : (v < -lim ? -lim : v);
+}
+
+static void one_trajectory2(const oracle_model *m, const oracle_table2 *tab, const oracle_bias *bias,
+                            double A2, uint64_t seed, uint32_t run_id, uint32_t traj,
+                            int64_t *nsteps, double *logw, uint8_t *status, double *phi_f,
+                            double *pi_f, double *xmin)
+{
+    const double dN = m->dN, sdN = sqrt(m->dN);
+    double phi = m->phi_in, pi = m->pi_in, lw = 0.0, xm = INFINITY;
+    double beta1 = 0.0, beta2 = 0.0;
+    if (bias->kind == 1) { beta1 = bias->A; beta2 = A2; }
+    double z[4];
+    int64_t n = 0;
+    int passed = 0;
+    while (n < m->max_steps) {
+        if ((n & 1) == 0)
+            oracle_normals4(seed, run_id, traj, (uint32_t)(n >> 1), z);
+        double xi1 = z[2 * (n & 1)], xi2 = z[2 * (n & 1) + 1];
+        double a, b, c;
+        table2_lookup(tab, phi, &a, &b, &c);
+        if (bias->kind == 2 && (n % bias->segment) == 0) {
+            double x = phi - m->phi_end;
+            if (bias->log_x) x = log(x > 1e-30 ? x : 1e-30);
+            double s[3] = {x, pi, (double)n * dN}, o[2];
+            oracle_mlp_forward(bias, s, o);
+            beta1 = clampd(o[0], bias->alpha_max);
+            beta2 = clampd(o[1], bias->alpha_max);
+        }
+        double B_phi = a * beta1 + b * beta2, B_pi = b * beta1 + c * beta2;   /* B = S beta */
+        double drift_pi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi));
+        double phi_new = phi + pi * dN + B_phi * dN + (a * xi1 + b * xi2) * sdN;
+        double pi_new = pi + drift_pi * dN + B_pi * dN + (b * xi1 + c * xi2) * sdN;
+        lw -= beta1 * (0.5 * beta1 * dN + xi1 * sdN) + beta2 * (0.5 * beta2 * dN + xi2 * sdN);
+        phi = phi_new;
+        pi = pi_new;
+        ++n;
+        if (phi <= m->phi_end) { passed = 1; break; }
+        double x = phi - m->phi_end;
+        if (x < xm) xm = x;
+    }
+    *nsteps = n;
+    *logw = lw;
+    *status = passed ? 0 : 1;
+    *phi_f = phi;
+    *pi_f = pi;
+    *xmin = xm;
+}
+
+int oracle_run2(const oracle_model *m, const oracle_table2 *tab, const oracle_bias *bias, double A2,
+                uint64_t seed, uint32_t run_id, int64_t traj0, int64_t n, int threads, oracle_out *out)
+{
+    if (!m || !tab || !bias || !out || n < 0 || tab->n_points < 2) return 1;
+    if (traj0 < 0 || traj0 + n > 4294967296LL) return 1;
+    if (bias->kind == 2 && bias->segment < 1) return 1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        one_trajectory2(m, tab, bias, A2, seed, run_id, (uint32_t)(traj0 + i), &out->nsteps[i],
+                        &out->logw[i], &out->status[i], &out->phi_final[i], &out->pi_final[i],
+                        &out->xmin_pre[i]);
+    }
+    return 0;
+}
+
 /* Run trajectories traj0 .. traj0+n-1 of one run. Returns 0 on success. */
 int oracle_run(const oracle_model *m, const oracle_table *tab,
                const oracle_bias *b, uint64_t seed, uint32_t run_id,

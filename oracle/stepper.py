@@ -51,6 +51,12 @@ class _Bias(C.Structure):
                 ("in_shift", C.c_double * 3), ("in_scale", C.c_double * 3)]
 
 
+class _Table2(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("phi_lo", C.c_double), ("h", C.c_double),
+                ("Spp", C.POINTER(C.c_double)), ("Spq", C.POINTER(C.c_double)),
+                ("Sqq", C.POINTER(C.c_double))]
+
+
 class _Out(C.Structure):
     _fields_ = [("nsteps", C.POINTER(C.c_int64)), ("logw", C.POINTER(C.c_double)),
                 ("status", C.POINTER(C.c_uint8)), ("phi_final", C.POINTER(C.c_double)),
@@ -83,6 +89,10 @@ def lib():
                                              C.POINTER(C.c_double), C.POINTER(C.c_uint8),
                                              C.POINTER(_Seg)]
         _lib.oracle_run_segments.restype = C.c_int
+        _lib.oracle_run2.argtypes = [C.POINTER(_Model), C.POINTER(_Table2), C.POINTER(_Bias),
+                                     C.c_double, C.c_uint64, C.c_uint32, C.c_int64, C.c_int64,
+                                     C.c_int, C.POINTER(_Out)]
+        _lib.oracle_run2.restype = C.c_int
         _lib.oracle_mlp_forward.argtypes = [C.POINTER(_Bias), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
         _lib.oracle_max_threads.restype = C.c_int
@@ -215,3 +225,27 @@ def mlp_forward_c(mlp: MLPBias, s):
 
 def max_threads() -> int:
     return int(lib().oracle_max_threads())
+
+
+def run2(m, resolved, table2, seed: int, run_id: int, n: int, traj0: int = 0, A: float = 0.0,
+         A2: float = 0.0, mlp: MLPBias | None = None, threads: int = 0) -> Trajectories:
+    """FP64 trajectories with full-rank 2-D noise (NoiseTable2); the bias is
+    B = S beta with beta = (A, A2), or the clamped MLP outputs."""
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (table2.Spp, table2.Spq, table2.Sqq)]
+    tab = _Table2(n_points=len(arrs[0]), phi_lo=table2.phi_lo, h=table2.h, Spp=_dp(arrs[0]),
+                  Spq=_dp(arrs[1]), Sqq=_dp(arrs[2]))
+    ms = model_struct(m, resolved.phi_in, resolved.pi_in, resolved.phi_end)
+    b = mlp.struct() if mlp is not None else bias_struct(A if (A != 0.0 or A2 != 0.0) else 0.0)
+    if mlp is None and A == 0.0 and A2 != 0.0:
+        b.kind = 1
+    out = dict(nsteps=np.zeros(n, np.int64), logw=np.zeros(n), status=np.zeros(n, np.uint8),
+               phi_final=np.zeros(n), pi_final=np.zeros(n), xmin_pre=np.zeros(n))
+    o = _Out(nsteps=out["nsteps"].ctypes.data_as(C.POINTER(C.c_int64)),
+             logw=_dp(out["logw"]), status=out["status"].ctypes.data_as(C.POINTER(C.c_uint8)),
+             phi_final=_dp(out["phi_final"]), pi_final=_dp(out["pi_final"]),
+             xmin_pre=_dp(out["xmin_pre"]))
+    rc = lib().oracle_run2(C.byref(ms), C.byref(tab), C.byref(b), float(A2), seed, run_id, traj0, n,
+                           threads, C.byref(o))
+    if rc != 0:
+        raise ValueError("oracle_run2 rejected its arguments")
+    return Trajectories(dN=m.dN, **out)

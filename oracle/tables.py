@@ -436,3 +436,67 @@ def consistency_ratio(m, res: Resolved, phi: float, sigma: float,
     phe, pie, _ = bg.state(Ne)
     P_full = abs(u_end) ** 2 / (pie * pie)          # |dphi|^2 / (2 eps1)
     return abs(C) ** 2 / P_full
+
+
+
+# --------------------------------------------------------------------------
+# Full-rank (2-D) noise: numerical matching, Eq. (3.9)
+# --------------------------------------------------------------------------
+@dataclass
+class NoiseTable2:
+    """phi-indexed 2x2 noise matrices S = sqrt(Xi) (symmetric): components
+    S_phiphi, S_phipi, S_pipi at phi_j = phi_lo + j h; end values held outside."""
+    phi_lo: float
+    h: float
+    Spp: np.ndarray
+    Spq: np.ndarray
+    Sqq: np.ndarray
+
+
+def sqrt_psd2(a, b, c):
+    """Symmetric square root of the PSD matrix [[a, b], [b, c]]:
+    S = (X + sqrt(det) I) / sqrt(tr + 2 sqrt(det))."""
+    det = max(a * c - b * b, 0.0)
+    sd = math.sqrt(det)
+    den = math.sqrt(a + c + 2.0 * sd)
+    if den == 0.0:
+        return 0.0, 0.0, 0.0
+    return (a + sd) / den, b / den, (c + sd) / den
+
+
+def xi_numeric_at_phi(m, res: Resolved, phi: float, sigma: float):
+    """Covariance of Eq. (3.9): the full mode delta phi_k and delta pi_k =
+    d(delta phi_k)/dN at k = sigma a H, Xi = k^3/(2 pi^2) (|dphi|^2,
+    Re(dphi dpi*), |dpi|^2). Returns (Xi_pp, Xi_pq, Xi_qq, a, H, k)."""
+    bg = res.bg
+    N_s = N_of_phi(bg, phi, bg.N_T, bg.N_max)
+    ph, pi, br = bg.state(N_s)
+    H = hubble(m, ph, pi, br)
+    k = sigma * math.exp(N_s) * H
+    N0 = N_s - math.log(BD_RATIO / sigma)
+    u, du, _ = mode_at(m, bg, k, N0, N_s)
+    # physical mode = u / (exp(N0) sqrt(2k))
+    norm = 1.0 / (math.exp(2.0 * N0) * 2.0 * k)
+    pref = k ** 3 / (2.0 * math.pi ** 2) * norm
+    xpp = pref * abs(u) ** 2
+    xpq = pref * (u * du.conjugate()).real
+    xqq = pref * abs(du) ** 2
+    return xpp, xpq, xqq, math.exp(N_s), H, k
+
+
+def numeric_table(m, res: Resolved, n_points: int, sigma: float, phi_lo=None, phi_hi=None,
+                  indices=None) -> NoiseTable2:
+    lo, hi = _table_range(res, phi_lo, phi_hi)
+    phis, h = grid(n_points, lo, hi)
+    idx = range(n_points) if indices is None else list(indices)
+    A = np.full(n_points, np.nan); B = np.full(n_points, np.nan); Cq = np.full(n_points, np.nan)
+    for j in idx:
+        xpp, xpq, xqq, _, _, _ = xi_numeric_at_phi(m, res, float(phis[j]), sigma)
+        A[j], B[j], Cq[j] = sqrt_psd2(xpp, xpq, xqq)
+    return NoiseTable2(lo, h, A, B, Cq)
+
+
+def user_table2(Spp, Spq, Sqq, phi_lo, phi_hi) -> NoiseTable2:
+    Spp = np.asarray(Spp, float)
+    return NoiseTable2(phi_lo, (phi_hi - phi_lo) / (len(Spp) - 1), Spp, np.asarray(Spq, float),
+                       np.asarray(Sqq, float))
