@@ -57,6 +57,11 @@ TAIL_P = 1e-12
 # ~40 shuffles/selects per lane = ~760, i.e. 6 per step. See the design doc.
 INSTR_PER_STEP = 60
 INSTR_PER_STEP_MLP = 66
+# Full-rank (2-D) stepper, per step: Philox (40 per 2 steps) 20, uniforms +
+# Box-Muller for 2 normals 16, two-entry table lookup + 3 interpolations 16,
+# drift 9, (phi, pi) update 8, field compensated add 4, log-weight (Kahan) 7,
+# counter + passage 5, predication 2.
+INSTR_PER_STEP_2D = 87
 # Training recipe of the learned proposal (log-variance loss towards
 # e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum).
 TRAIN = dict(rounds=300, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4)
@@ -211,6 +216,75 @@ def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
     return prop, time.perf_counter() - t0
 
 
+def peak_pdf(fpt, ctx, run, stream, N_lo, N_hi, bins=48):
+    h = fpt.fpt_histogram(ctx, run, N_lo, N_hi, bins, stream=stream)
+    return np.asarray(h["pdf"]), np.asarray(h["se_jk"]), h["N_mean"]
+
+
+def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm_max):
+    """Full-rank noise (numerical matching of Eq. 3.9 at sigma = 1, 4096
+    points) on the same model: direct-sampling throughput of the 2-D stepper,
+    its issue roofline, the tail ESS rate with the constant standardised bias
+    beta = (A, 0), and the 1-D vs 2-D comparison of P(delta N) near the peak
+    (direct runs, same sigma)."""
+    nd = 1 << 22
+    out = {"table": "numerical matching, sigma = 1, 4096 points", "n_traj_per_run": nd}
+    ctx2 = fpt.fpt_init_model([m, m], device=torch.cuda.current_device())
+    t0 = time.perf_counter()
+    fpt.fpt_noise_table2(ctx2, 0, fpt.FPT_TABLE_NUMERIC, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
+    out["table_build_s"] = round(time.perf_counter() - t0, 3)
+    fpt.fpt_noise_table(ctx2, 1, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
+    fpt.fpt_autotune(ctx2, [fpt.run_desc(0, nd, seed=seed + 5, run_id=99)], fraction=0.25)
+    d2 = lambda k, A_=0.0: fpt.run_desc(0, nd, seed=seed + 5, run_id=k, A=A_, traj_offset=rank * nd)
+    fpt.fpt_run(ctx2, [d2(100)], stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 0.0
+    ms = []
+    for k in range(3):
+        e0.record(stream)
+        fpt.fpt_run(ctx2, [d2(k)], stream=stream)
+        e1.record(stream)
+        h = fpt.fpt_histogram(ctx2, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        steps += h["N_mean"] * h["n_passed"] / m.dN
+    t = sum(ms) * 1e-3
+    out["direct_traj_per_s"] = 3 * nd / t
+    out["em_steps_per_s"] = steps / t
+    out["roofline"] = roofline(steps / 3, float(np.mean(ms)), sm_count, sm_max, None, INSTR_PER_STEP_2D)
+    out["roofline"]["kernel"] = "em2_kernel<direct, smem table>"
+    # 1-D vs 2-D near the peak: the same seed range, direct sampling
+    pdf2, se2, mean2 = peak_pdf(fpt, ctx2, 0, stream, 4.0, 6.0)
+    fpt.fpt_run(ctx2, [fpt.run_desc(1, nd, seed=seed + 6, run_id=0, traj_offset=rank * nd)], stream=stream)
+    pdf1, se1, mean1 = peak_pdf(fpt, ctx2, 0, stream, 4.0, 6.0)
+    ok = (se1 > 0) & (se2 > 0) & (pdf1 > 1e-3 * pdf1.max())
+    z = np.abs(pdf2 - pdf1)[ok] / np.hypot(se1, se2)[ok]
+    out["peak_1d_vs_2d"] = {"N_mean_1d": mean1, "N_mean_2d": mean2,
+                            "pdf_max_1d": float(pdf1.max()), "pdf_max_2d": float(pdf2.max()),
+                            "max_abs_z": float(z.max()) if z.size else None, "bins": int(ok.sum()),
+                            "range": [4.0, 6.0]}
+    # importance sampling on 2-D noise: beta = (A, 0)
+    nb = 1 << 22
+    fpt.fpt_run(ctx2, [fpt.run_desc(0, nb, seed=seed + 7, run_id=50, A=A, traj_offset=rank * nb)],
+                stream=stream)
+    e0.record(stream)
+    sw = sw2 = 0.0
+    for k in range(3):
+        fpt.fpt_run(ctx2, [fpt.run_desc(0, nb, seed=seed + 7, run_id=k, A=A, traj_offset=rank * nb)],
+                    stream=stream)
+        h = fpt.fpt_histogram(ctx2, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        a, b = shard.tail_sums(h)
+        sw += a
+        sw2 += b
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["fixed_bias"] = {"beta": [A, 0.0], "n_traj_per_run": nb,
+                         "ess_tail_per_s": shard.ess_of(sw, sw2) / (e0.elapsed_time(e1) * 1e-3)}
+    fpt.fpt_sync(ctx2)
+    ctx2.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +299,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / judge / direct legs")
+    ap.add_argument("--no-2d", action="store_true", help="skip the full-rank (2-D) noise leg")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -373,6 +448,10 @@ def main():
         torch.cuda.synchronize()
         direct_traj_s = 3 * nd / (e0.elapsed_time(e1) * 1e-3)
         extras["direct"] = {"traj_per_s": direct_traj_s * world, "ess_tail_per_s": direct_traj_s * TAIL_P * world}
+        if not args.no_2d:
+            sm_max_2d = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+            extras["noise_2d"] = noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
+                                              sm_count, sm_max_2d)
 
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0

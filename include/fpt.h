@@ -73,7 +73,11 @@ enum {
      * For these kinds phi_lo / phi_hi carry N_lo / N_hi (required). */
     FPT_TABLE_BESSEL_N = 3,  /* Bessel-matched noise of the mode crossing sigma a H
                                 at background time N_in + N                   */
-    FPT_TABLE_USER_N = 4     /* caller-supplied S(N_j), S_pi(N_j)            */
+    FPT_TABLE_USER_N = 4,    /* caller-supplied S(N_j), S_pi(N_j)            */
+    /* Full-rank (2-D) tables (fpt_noise_table2), phi-indexed: */
+    FPT_TABLE_NUMERIC = 5,   /* numerical matching, Eq. (3.9): Xi of the full
+                                mode at k = sigma a H, S = sqrt(Xi) (symmetric) */
+    FPT_TABLE_USER2 = 6      /* caller-supplied symmetric S(phi_j)           */
 };
 
 /* Bias kinds (fpt_run_desc.bias_kind). */
@@ -164,13 +168,39 @@ fpt_status fpt_noise_table(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_
                            double *out_S, double *out_Spi);
 
 /*
+ * Full-rank (2-D) noise table of model `model` (Sec. 3.3): the noise of the
+ * Langevin system Eq. (2.24) is S xi sqrt(dN) with two independent normals
+ * xi = (xi_1, xi_2) per step and the symmetric 2x2 matrix
+ * S = [[S_phiphi, S_phipi], [S_phipi, S_pipi]], covariance Xi = S^2.
+ * Grid and interpolation as fpt_noise_table (phi-indexed, end values held).
+ *
+ * kind FPT_TABLE_NUMERIC: for each phi_j the mode of k_j = sigma a H at N_j
+ *   (phi_bg(N_j) = phi_j), from its Bunch-Davies state at N_j - ln(100/sigma)
+ *   through the kink; Xi = k^3/(2 pi^2) (|dphi|^2, Re(dphi dpi*), |dpi|^2),
+ *   dpi = d(dphi)/dN; S = sqrt(Xi). Requires the transition rule and
+ *   0 < sigma <= 10. The paper uses sigma << 1 for this matching.
+ * kind FPT_TABLE_USER2: user_S (host) holds 3 n_points doubles, the planes
+ *   S_phiphi[n_points], S_phipi[n_points], S_pipi[n_points] (finite).
+ * out_S: optional host buffer of 3 n_points doubles (same planes).
+ * A model holds one table: this call replaces a 1-D table and vice versa.
+ * Runs on a 2-D table use the 2-D stepper (see fpt_run_desc). Blocks until
+ * the upload finished.
+ */
+fpt_status fpt_noise_table2(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_points,
+                            double sigma, double phi_lo, double phi_hi, const double *user_S,
+                            double *out_S);
+
+/*
  * Host-only helpers (no context, no GPU): the same FP64 model resolution and
- * table construction that fpt_init_model / fpt_noise_table use.
+ * table construction that fpt_init_model / fpt_noise_table(2) use.
+ * fpt_table_build2 builds FPT_TABLE_NUMERIC only (out_S: 3 n_points doubles).
  */
 fpt_status fpt_resolve_model(const fpt_model *model, fpt_model_info *out);
 fpt_status fpt_table_build(const fpt_model *model, int32_t kind, int32_t n_points,
                            double sigma, double phi_lo, double phi_hi,
                            double *out_S, double *out_Spi);
+fpt_status fpt_table_build2(const fpt_model *model, int32_t kind, int32_t n_points,
+                            double sigma, double phi_lo, double phi_hi, double *out_S);
 
 /*
  * One run: a set of trajectories of one model with one bias.
@@ -207,6 +237,7 @@ typedef struct {
     int32_t mlp_flags;      /* FPT_BIAS_MLP: FPT_MLP_LOG_X = first input is
                                ln(max(phi - phi_end, 1e-30)) instead of
                                phi - phi_end                                 */
+    double A2;              /* FPT_BIAS_CONST on 2-D tables: beta_2          */
 } fpt_run_desc;
 
 enum { FPT_MLP_LOG_X = 1 };

@@ -31,9 +31,12 @@ std::string g_init_err = "no error";
 struct TableHost {
     bool ready = false;
     bool n_indexed = false;    // grid in time since the start (noise window)
+    bool rank2 = false;        // full-rank 2-D noise: S = S_phiphi, T = S_phipi, C = S_pipi
     int M = 0;
     double lo = 0, h = 0;
-    std::vector<double> S, T;
+    std::vector<double> S, T, C;
+    // float4 entries on the device: M (1-D: value + slope) or M + 1 (2-D: values)
+    int entries() const { return rank2 ? M + 1 : M; }
 };
 
 using GraphKey = std::tuple<int, int, int, int, size_t, int, int, int, long long, int>;
@@ -302,6 +305,78 @@ fpt_status fpt_table_build(const fpt_model *model, int32_t kind, int32_t n_point
     return FPT_OK;
 }
 
+// Full-rank (2-D) tables: arguments, host build and the copy-out of the
+// three planes (S_phiphi, S_phipi, S_pipi).
+static fpt_status table2_args(int kind, int n_points, double sigma, double phi_lo, double phi_hi,
+                              const double *uS, std::string &msg)
+{
+    if (kind != FPT_TABLE_NUMERIC && kind != FPT_TABLE_USER2) { msg = "unknown 2-D table kind"; return FPT_E_INVALID; }
+    if (n_points < 2 || n_points > kMaxTablePoints) { msg = "n_points out of [2, 8192]"; return FPT_E_INVALID; }
+    if (std::isnan(phi_lo) != std::isnan(phi_hi)) { msg = "phi_lo and phi_hi must both be set or both NaN"; return FPT_E_INVALID; }
+    if (!std::isnan(phi_lo) && !(phi_hi > phi_lo && std::isfinite(phi_lo) && std::isfinite(phi_hi))) {
+        msg = "need finite phi_lo < phi_hi";
+        return FPT_E_INVALID;
+    }
+    if (kind == FPT_TABLE_NUMERIC && !(sigma > 0 && sigma <= 10)) { msg = "sigma out of (0, 10]"; return FPT_E_INVALID; }
+    if (kind == FPT_TABLE_USER2) {
+        if (!uS) { msg = "USER2 tables need user_S"; return FPT_E_INVALID; }
+        for (int j = 0; j < 3 * n_points; ++j)
+            if (!std::isfinite(uS[j])) { msg = "USER2 table values must be finite"; return FPT_E_INVALID; }
+    }
+    return FPT_OK;
+}
+
+static fpt_status build_host_table2(const fpt_model &m, const fpt_model_info &info, int kind,
+                                    int n_points, double sigma, double phi_lo, double phi_hi,
+                                    const double *uS, TableHost &t, std::string &msg)
+{
+    try {
+        if (kind == FPT_TABLE_USER2) {
+            double lo = std::isnan(phi_lo) ? info.phi_end : phi_lo;
+            double hi = std::isnan(phi_hi) ? info.phi_in : phi_hi;
+            if (!(hi > lo)) { msg = "need phi_hi > phi_lo"; return FPT_E_INVALID; }
+            t.S.assign(uS, uS + n_points);
+            t.T.assign(uS + n_points, uS + 2 * n_points);
+            t.C.assign(uS + 2 * n_points, uS + 3 * n_points);
+            t.lo = lo;
+            t.h = (hi - lo) / (n_points - 1);
+        } else {
+            fpt_host::build_table2(m, kind, n_points, sigma, phi_lo, phi_hi, t.S, t.T, t.C, t.lo, t.h);
+        }
+    } catch (const std::exception &e) {
+        msg = e.what();
+        return FPT_E_INVALID;
+    }
+    t.M = n_points;
+    t.ready = true;
+    t.rank2 = true;
+    return FPT_OK;
+}
+
+static void copy_planes(const TableHost &t, double *out)
+{
+    std::copy(t.S.begin(), t.S.end(), out);
+    std::copy(t.T.begin(), t.T.end(), out + t.M);
+    std::copy(t.C.begin(), t.C.end(), out + 2 * t.M);
+}
+
+fpt_status fpt_table_build2(const fpt_model *model, int32_t kind, int32_t n_points, double sigma,
+                            double phi_lo, double phi_hi, double *out_S)
+{
+    if (!model || !out_S) return fail(nullptr, FPT_E_INVALID, "null argument");
+    if (kind != FPT_TABLE_NUMERIC) return fail(nullptr, FPT_E_INVALID, "only NUMERIC tables are built");
+    std::string msg;
+    fpt_status s = table2_args(kind, n_points, sigma, phi_lo, phi_hi, nullptr, msg);
+    if (s != FPT_OK) return fail(nullptr, s, msg);
+    fpt_model_info info;
+    if ((s = fpt_resolve_model(model, &info)) != FPT_OK) return s;
+    TableHost t;
+    s = build_host_table2(*model, info, kind, n_points, sigma, phi_lo, phi_hi, nullptr, t, msg);
+    if (s != FPT_OK) return fail(nullptr, s, msg);
+    copy_planes(t, out_S);
+    return FPT_OK;
+}
+
 fpt_status fpt_init_model(fpt_ctx **pctx, const fpt_model *models, int32_t n_models, int32_t device)
 {
     if (!pctx) return fail(nullptr, FPT_E_INVALID, "null ctx pointer");
@@ -373,7 +448,7 @@ static fpt_status upload_tables(fpt_ctx *ctx)
     size_t total = 0;
     for (size_t i = 0; i < ctx->tables.size(); ++i) {
         ctx->table_offset[i] = (int)total;
-        if (ctx->tables[i].ready) total += ctx->tables[i].M;
+        if (ctx->tables[i].ready) total += ctx->tables[i].entries();
     }
     std::vector<float4> packed(std::max<size_t>(total, 1));
     std::vector<ModelDev> md(ctx->models.size());
@@ -415,6 +490,16 @@ static fpt_status upload_tables(fpt_ctx *ctx)
                 d.u_shift = (float)((inf.phi_end - t.lo) / t.h);
             }
             const double sq = std::sqrt(m.dN);
+            d.rank2 = t.rank2 ? 1 : 0;
+            if (t.rank2) {
+                // (S_phiphi, S_phipi, S_pipi, 0) sqrt(dN); entry M repeats entry M - 1
+                for (int j = 0; j <= t.M; ++j) {
+                    const int k = std::min(j, t.M - 1);
+                    packed[ctx->table_offset[i] + j] =
+                        make_float4((float)(t.S[k] * sq), (float)(t.T[k] * sq), (float)(t.C[k] * sq), 0.0f);
+                }
+                continue;
+            }
             for (int j = 0; j < t.M; ++j) {
                 const int k = std::min(j + 1, t.M - 1);
                 float4 e;
@@ -461,6 +546,27 @@ fpt_status fpt_noise_table(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_
     if ((s = upload_tables(ctx)) != FPT_OK) return s;
     if (out_S) std::copy(t.S.begin(), t.S.end(), out_S);
     if (out_Spi) std::copy(t.T.begin(), t.T.end(), out_Spi);
+    return FPT_OK;
+}
+
+fpt_status fpt_noise_table2(fpt_ctx *ctx, int32_t model, int32_t kind, int32_t n_points,
+                            double sigma, double phi_lo, double phi_hi, const double *user_S,
+                            double *out_S)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (model < 0 || model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "model index out of range");
+    std::string msg;
+    fpt_status s = table2_args(kind, n_points, sigma, phi_lo, phi_hi, user_S, msg);
+    if (s != FPT_OK) return fail(ctx, s, msg);
+    TableHost t;
+    s = build_host_table2(ctx->models[model], ctx->infos[model], kind, n_points, sigma, phi_lo, phi_hi,
+                          user_S, t, msg);
+    if (s != FPT_OK) return fail(ctx, s, msg);
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
+    ctx->tables[model] = t;
+    if ((s = upload_tables(ctx)) != FPT_OK) return s;
+    if (out_S) copy_planes(t, out_S);
     return FPT_OK;
 }
 
@@ -531,6 +637,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     long long total = 0;
     bool weighted = false;
     bool nidx = false;
+    int rank2 = -1;
     int mlp_run = -1;
     for (int r = 0; r < n_runs; ++r) {
         const fpt_run_desc &d = runs[r];
@@ -557,12 +664,22 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
                 std::memcmp(d.mlp_scale, q.mlp_scale, sizeof(q.mlp_scale)))
                 return fail(ctx, FPT_E_INVALID, "all MLP runs of one call must share one proposal");
         }
-        if (d.bias_kind == FPT_BIAS_CONST && !std::isfinite(d.A)) return fail(ctx, FPT_E_INVALID, "A must be finite");
+        if (d.bias_kind == FPT_BIAS_CONST && (!std::isfinite(d.A) || !std::isfinite(d.A2)))
+            return fail(ctx, FPT_E_INVALID, "A and A2 must be finite");
+        if (d.n_traj > 0) {
+            const bool r2 = ctx->tables[d.model].rank2;
+            if (rank2 < 0) rank2 = r2 ? 1 : 0;
+            else if (rank2 != (r2 ? 1 : 0))
+                return fail(ctx, FPT_E_INVALID, "runs of one call must all use 1-D or all use 2-D noise tables");
+            if (!r2 && d.bias_kind == FPT_BIAS_CONST && d.A2 != 0.0)
+                return fail(ctx, FPT_E_INVALID, "A2 needs a 2-D noise table");
+        }
         if (d.n_traj < 0 || d.traj_offset < 0 || d.traj_offset + d.n_traj > (1LL << 32))
             return fail(ctx, FPT_E_INVALID, "trajectory ids must lie in [0, 2^32)");
         if (d.seed != runs[0].seed) return fail(ctx, FPT_E_INVALID, "all runs of one call must share the seed");
         if (d.n_traj > 0) used_models.insert(d.model);
-        if ((d.bias_kind == FPT_BIAS_CONST && d.A != 0.0) || d.bias_kind == FPT_BIAS_MLP) weighted = true;
+        if ((d.bias_kind == FPT_BIAS_CONST && (d.A != 0.0 || d.A2 != 0.0)) || d.bias_kind == FPT_BIAS_MLP)
+            weighted = true;
         if (d.n_traj > 0 && ctx->tables[d.model].n_indexed) {
             if (d.bias_kind == FPT_BIAS_MLP)
                 return fail(ctx, FPT_E_INVALID, "learned-proposal runs need a phi-indexed noise table");
@@ -584,10 +701,12 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
         RunDev &rd = ctx->last_runs[r];
         std::memset(&rd, 0, sizeof(rd));
         const double A = d.bias_kind == FPT_BIAS_CONST ? d.A : 0.0;
+        const double A2 = d.bias_kind == FPT_BIAS_CONST ? d.A2 : 0.0;
         rd.model = d.model;
         rd.bias_kind = d.bias_kind;
         rd.cb = (float)(A * std::sqrt(m.dN));
-        rd.half_cb2 = (float)(0.5 * A * A * m.dN);
+        rd.cb_b = (float)(A2 * std::sqrt(m.dN));
+        rd.half_cb2 = (float)(0.5 * (A * A + A2 * A2) * m.dN);
         rd.n_traj = d.n_traj;
         rd.traj_offset = d.traj_offset;
         rd.unit_begin = begin;
@@ -610,8 +729,10 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const bool smem = used_models.size() == 1;
     const int smem_model = smem ? *used_models.begin() : 0;
     const bool mlp = mlp_run >= 0;
-    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp};
-    const size_t smem_bytes = (smem ? sizeof(float4) * ctx->tables[smem_model].M : 0) +
+    if (mlp && ctx->record_mode && rank2 == 1)
+        return fail(ctx, FPT_E_INVALID, "training records need a 1-D noise table");
+    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1};
+    const size_t smem_bytes = (smem ? sizeof(float4) * ctx->tables[smem_model].entries() : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
     // the learned-proposal stepper is compiled for at most kMlpMaxBlock threads
     const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
@@ -630,7 +751,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     p.n_runs = n_runs;
     p.tables = ctx->d_tables;
     p.smem_table_offset = smem ? ctx->table_offset[smem_model] : 0;
-    p.smem_table_points = smem ? ctx->tables[smem_model].M : 0;
+    p.smem_table_points = smem ? ctx->tables[smem_model].entries() : 0;
     p.total_units = total;
     p.cursor = ctx->d_cursor;
     p.flags = ctx->d_flags;
@@ -652,7 +773,8 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
         if (graph) {
             GraphKey key{weighted, smem, grid, block, smem_bytes, p.groups_per_check, n_runs,
                          smem ? smem_model : -1, total,
-                         (mlp ? 1 : 0) + (var.rec ? 2 : 0) + (var.nidx ? 4 : 0) + 8 * p.mlp_run};
+                         (mlp ? 1 : 0) + (var.rec ? 2 : 0) + (var.nidx ? 4 : 0) + (var.rank2 ? 8 : 0) +
+                             16 * p.mlp_run};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 cudaGraph_t g;

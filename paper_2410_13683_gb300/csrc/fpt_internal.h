@@ -18,6 +18,9 @@ fpt_model_info resolve(const fpt_model &m);
 void build_table(const fpt_model &m, int kind, int n_points, double sigma, double phi_lo,
                  double phi_hi, std::vector<double> &S, std::vector<double> &Spi,
                  double &lo_out, double &h_out);
+void build_table2(const fpt_model &m, int kind, int n_points, double sigma, double phi_lo,
+                  double phi_hi, std::vector<double> &Spp, std::vector<double> &Spq,
+                  std::vector<double> &Sqq, double &lo_out, double &h_out);
 double dlnV(const fpt_model &m, double phi, int branch);
 double Vof(const fpt_model &m, double phi, int branch);
 double hubble(const fpt_model &m, double phi, double pi, int branch);
@@ -46,6 +49,7 @@ struct ModelDev {
     int32_t max_steps;
     int32_t table_offset;      // first float4 entry of this model's table
     int32_t nidx;              // 1: table indexed by the step count (noise window)
+    int32_t rank2;             // 1: full-rank 2-D noise table (M + 1 entries)
     int32_t win_lo, win_hi;    // noise window [win_lo, win_hi] in steps (nidx)
 };
 
@@ -53,8 +57,9 @@ struct ModelDev {
 struct RunDev {
     int32_t model;
     int32_t bias_kind;
-    float cb;                  // A sqrt(dN)
-    float half_cb2;            // A^2 dN / 2
+    float cb;                  // A sqrt(dN) (2-D noise: beta_1 sqrt(dN))
+    float half_cb2;            // A^2 dN / 2 (2-D noise: |beta|^2 dN / 2)
+    float cb_b;                // 2-D noise: beta_2 sqrt(dN)
     long long n_traj;
     long long traj_offset;
     long long unit_begin;      // first launch unit of this run
@@ -119,6 +124,7 @@ enum {
 // proposal, segment records.
 struct EmVariant {
     bool weighted, smem, mlp, rec, nidx;
+    bool rank2;              // full-rank 2-D noise stepper
 };
 
 // Host wrappers implemented in fpt_kernels.cu.

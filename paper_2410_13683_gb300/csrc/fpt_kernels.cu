@@ -88,7 +88,7 @@ __device__ __forceinline__ void kahan_add(float &hi, float &lo, float v)
 struct RunSm {               // per-run constants staged in shared memory
     long long unit_begin;
     long long traj_offset;
-    float cb, half_cb2;
+    float cb, half_cb2, cb_b;
     uint32_t run_id;
     int32_t model;
     int32_t is_mlp;
@@ -102,6 +102,7 @@ struct Lane {                // per-thread trajectory state and its constants
     int nmax;
     uint32_t traj, run_id;
     float cb, half_cb2, dN, sqrt_dN;
+    float cb_b;              // 2-D noise: beta_2 sqrt(dN) (cb = beta_1 sqrt(dN))
     float x_star, a_plus, a_minus, b_plus, b_minus;
     float u_scale, u_shift, u_max;
     int tbase;
@@ -133,6 +134,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.run_id = r.run_id;
     L.cb = r.cb;
     L.half_cb2 = r.half_cb2;
+    L.cb_b = r.cb_b;
     L.mlp = r.is_mlp != 0;
     L.dN = m.dN;
     L.sqrt_dN = r.sqrt_dN;
@@ -255,17 +257,14 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
     }
 }
 
-// Register budgets: the plain stepper keeps three 512-thread blocks per SM
-// (48 warps); the learned-proposal stepper at most 384 threads per block and
-// two resident blocks, so that the network's registers still leave 24 warps.
-template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX>
-__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 3) em_kernel(const EmParams P)
+// Launch prologue shared by the steppers: clock origin, per-run and per-model
+// constants, the table (SMEM variants) and the proposal blob (MLP variants)
+// staged in shared memory. `table_entries` float4 entries are staged.
+template <bool SMEM, bool MLP>
+__device__ __forceinline__ void stage_launch(const EmParams &P, float4 *s_tab, RunSm *s_run,
+                                             ModelDev *s_model, unsigned long long &s_t0,
+                                             uint2 *s_tiles)
 {
-    extern __shared__ __align__(16) float4 s_tab[];
-    __shared__ RunSm s_run[kMaxRuns];
-    __shared__ ModelDev s_model[kMaxModels];
-    __shared__ unsigned long long s_t0;
-
     if (P.budget_ns && threadIdx.x == 0) {
         // the launch's clock origin: the first block to start sets it
         const unsigned long long now = globaltimer();
@@ -278,6 +277,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 
         s_run[i].traj_offset = r.traj_offset;
         s_run[i].cb = r.cb;
         s_run[i].half_cb2 = r.half_cb2;
+        s_run[i].cb_b = r.cb_b;
         s_run[i].run_id = r.run_id;
         s_run[i].model = r.model;
         s_run[i].is_mlp = r.bias_kind == FPT_BIAS_MLP;
@@ -289,16 +289,84 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 
         const float4 *src = P.tables + P.smem_table_offset;
         for (int i = threadIdx.x; i < P.smem_table_points; i += blockDim.x) s_tab[i] = src[i];
     }
-    // MLP variants: the proposal's fragment blob follows the table in shared memory
-    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + (SMEM ? P.smem_table_points : 0));
-    float *s_bias = reinterpret_cast<float *>(s_tiles + kMlpTiles * 32);
-    const RunDev &prun = P.runs[MLP ? P.mlp_run : 0];
     if (MLP) {
-        const float4 *src = reinterpret_cast<const float4 *>(prun.mlp);
+        const float4 *src = reinterpret_cast<const float4 *>(P.runs[P.mlp_run].mlp);
         float4 *dst = reinterpret_cast<float4 *>(s_tiles);
         for (int i = threadIdx.x; i < kMlpBlobBytes / 16; i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+}
+
+// Refill point: write the warp's finished trajectories and fetch new units
+// with one warp-aggregated atomic on the work cursor.
+__device__ __forceinline__ void refill_point(const EmParams &P, Lane &L, bool &active, bool &done,
+                                             const RunSm *s_run, const ModelDev *s_model)
+{
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const bool fin_me = active && done;
+    const unsigned fin = __ballot_sync(FULL, fin_me);
+    if (!fin) return;
+    if (fin_me) {
+        const bool passed = __fsub_rn(L.x, L.x_c) <= 0.0f;
+        P.nsteps[L.unit] = L.n;
+        P.logw[L.unit] = (double)L.lw_hi + (double)L.lw_lo;
+        P.status[L.unit] = passed ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
+        if (!passed) atomicAdd(P.flags + 1, 1);
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(P.cursor, (unsigned long long)__popc(fin));
+    base = __shfl_sync(FULL, base, 0);
+    if (fin_me) {
+        const long long unit = (long long)(base + __popc(fin & ((1u << lane) - 1u)));
+        done = false;
+        active = unit < P.total_units;
+        if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
+    }
+}
+
+// First units of a warp.
+__device__ __forceinline__ void first_units(const EmParams &P, Lane &L, bool &active,
+                                            const RunSm *s_run, const ModelDev *s_model)
+{
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(P.cursor, 32ull);
+    base = __shfl_sync(FULL, base, 0);
+    const long long unit = (long long)(base + lane);
+    active = unit < P.total_units;
+    if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
+    else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false, L.nidx = false;
+}
+
+// Deadline: true when the launch should stop (lane 0 reads the device clock).
+__device__ __forceinline__ bool past_deadline(const EmParams &P, unsigned long long t0)
+{
+    int stop = 0;
+    if ((threadIdx.x & 31u) == 0) {
+        if (globaltimer() - t0 > P.budget_ns) atomicExch(P.flags, 1);
+        stop = *(volatile int *)P.flags;
+    }
+    return __shfl_sync(0xffffffffu, stop, 0) != 0;
+}
+
+// Register budgets: the plain stepper keeps three 512-thread blocks per SM
+// (48 warps); the learned-proposal stepper at most 384 threads per block and
+// two resident blocks, so that the network's registers still leave 24 warps.
+template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX>
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 3) em_kernel(const EmParams P)
+{
+    extern __shared__ __align__(16) float4 s_tab[];
+    __shared__ RunSm s_run[kMaxRuns];
+    __shared__ ModelDev s_model[kMaxModels];
+    __shared__ unsigned long long s_t0;
+
+    // MLP variants: the proposal's fragment blob follows the table in shared memory
+    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + (SMEM ? P.smem_table_points : 0));
+    float *s_bias = reinterpret_cast<float *>(s_tiles + kMlpTiles * 32);
+    const RunDev &prun = P.runs[MLP ? P.mlp_run : 0];
+    stage_launch<SMEM, MLP>(P, s_tab, s_run, s_model, s_t0, s_tiles);
 
     const float4 *tab = SMEM ? s_tab : P.tables;
     const unsigned lane = threadIdx.x & 31u;
@@ -308,15 +376,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 
     SegRec sg;
     sg.open = false;
     bool active = false, done = false;
-    {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(P.cursor, 32ull);
-        base = __shfl_sync(FULL, base, 0);
-        const long long unit = (long long)(base + lane);
-        active = unit < P.total_units;
-        if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
-        else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false, L.nidx = false;
-    }
+    first_units(P, L, active, s_run, s_model);
 
     for (;;) {
         if (MLP && __any_sync(FULL, active && L.mlp))
@@ -360,43 +420,134 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 
         }
 
         // refill point: write finished trajectories, fetch new work
-        const bool fin_me = active && done;
-        const unsigned fin = __ballot_sync(FULL, fin_me);
-        if (fin) {
-            if (fin_me) {
-                const bool passed = __fsub_rn(L.x, L.x_c) <= 0.0f;
-                P.nsteps[L.unit] = L.n;
-                P.logw[L.unit] = (double)L.lw_hi + (double)L.lw_lo;
-                P.status[L.unit] = passed ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
-                if (!passed) atomicAdd(P.flags + 1, 1);
-            }
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(P.cursor, (unsigned long long)__popc(fin));
-            base = __shfl_sync(FULL, base, 0);
-            if (fin_me) {
-                const long long unit = (long long)(base + __popc(fin & ((1u << lane) - 1u)));
-                done = false;
-                active = unit < P.total_units;
-                if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
-            }
-        }
+        refill_point(P, L, active, done, s_run, s_model);
         if (!__any_sync(FULL, active)) break;
-        if (P.budget_ns) {
-            int stop = 0;
-            if (lane == 0) {
-                if (globaltimer() - s_t0 > P.budget_ns) atomicExch(P.flags, 1);
-                stop = *(volatile int *)P.flags;
-            }
-            if (__shfl_sync(FULL, stop, 0)) {
-                // trajectories in flight keep the ABORTED status set before launch
-                break;
+        // trajectories in flight keep the ABORTED status set before launch
+        if (P.budget_ns && past_deadline(P, s_t0)) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1b: full-rank (2-D) noise stepper
+// ---------------------------------------------------------------------------
+// Euler-Maruyama of Eq. (2.24) with the symmetric noise matrix S = sqrt(Xi)
+// (Eq. 3.9): two normals per step, step n using normals 2(n & 1), 2(n & 1) + 1
+// of Philox block n >> 1. Bias in standardised form B = S beta, so that
+// Eq. (4.5) reduces to dA = beta . (beta dN/2 + xi sqrt(dN)) (S^T Xi^-1 S = 1).
+// Table: M + 1 float4 entries (S_phiphi, S_phipi, S_pipi, 0) sqrt(dN) at the
+// grid points, entry M repeating entry M - 1; linear interpolation reads
+// entries k and k + 1.
+template <bool SMEM>
+__device__ __forceinline__ void table2_at(const Lane &L, const float4 *__restrict__ tab, float &a,
+                                          float &b, float &c)
+{
+    const float kMagic = 12582912.0f;                        // 1.5 * 2^23
+    float u = fmaf(L.x, L.u_scale, L.u_shift);
+    u = fminf(fmaxf(u, 0.0f), L.u_max);
+    const float t = (u - 0.5f) + kMagic;
+    const int i = __float_as_int(t) - 0x4b400000;
+    const float f = u - (t - kMagic);
+    const float4 e0 = SMEM ? tab[i] : __ldg(tab + L.tbase + i);
+    const float4 e1 = SMEM ? tab[i + 1] : __ldg(tab + L.tbase + i + 1);
+    a = fmaf(f, e1.x - e0.x, e0.x);
+    b = fmaf(f, e1.y - e0.y, e0.y);
+    c = fmaf(f, e1.z - e0.z, e0.z);
+}
+
+template <bool WEIGHTED, bool SMEM>
+__device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const float4 *__restrict__ tab)
+{
+    float a, b, c;                                       // S sqrt(dN), interpolated in x
+    table2_at<SMEM>(L, tab, a, b, c);
+    const float d = L.x - L.x_star;
+    const bool up = d >= 0.0f;
+    const float sa = up ? L.a_plus : L.a_minus;
+    const float sb = up ? L.b_plus : L.b_minus;
+    const float vpv = __fdividef(sa, fmaf(sb, d, 1.0f));
+    const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
+    const float e1 = z1 + L.cb, e2 = z2 + L.cb_b;       // xi + beta sqrt(dN)
+    // (phi, pi) += D dN + S beta dN + S xi sqrt(dN) = D dN + (S sqrt(dN)) e
+    const float dx = fmaf(a, e1, fmaf(b, e2, L.p * L.dN));
+    const float pn = fmaf(b, e1, fmaf(c, e2, fmaf(hh * L.dN, L.p + vpv, L.p)));
+    if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2)));
+    kahan_add(L.x, L.x_c, dx);
+    L.p = pn;
+    ++L.n;
+    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= L.nmax);
+}
+
+// Learned proposal in 2-D: beta = (clamp(o1), clamp(o2)) at the segment start.
+__device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, const uint2 *tiles,
+                                                   const float *bias, const RunDev &pr)
+{
+    float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f;
+    if (live) {
+        const float xv = __fsub_rn(L.x, L.x_c);
+        in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
+        in0 = (in0 - pr.shift[0]) * pr.scale[0];
+        in1 = (L.p - pr.shift[1]) * pr.scale[1];
+        in2 = ((float)L.n * L.dN - pr.shift[2]) * pr.scale[2];
+    }
+    float o1, o2;
+    mlp_forward_warp(tiles, bias, in0, in1, in2, o1, o2);
+    if (live) {
+        const float b1 = fminf(fmaxf(o1, -pr.alpha_max), pr.alpha_max);
+        const float b2 = fminf(fmaxf(o2, -pr.alpha_max), pr.alpha_max);
+        L.cb = b1 * L.sqrt_dN;
+        L.cb_b = b2 * L.sqrt_dN;
+        L.half_cb2 = 0.5f * fmaf(b1, b1, b2 * b2) * L.dN;
+    }
+}
+
+template <bool WEIGHTED, bool SMEM, bool MLP>
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
+{
+    extern __shared__ __align__(16) float4 s_tab[];
+    __shared__ RunSm s_run[kMaxRuns];
+    __shared__ ModelDev s_model[kMaxModels];
+    __shared__ unsigned long long s_t0;
+
+    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + (SMEM ? P.smem_table_points : 0));
+    float *s_bias = reinterpret_cast<float *>(s_tiles + kMlpTiles * 32);
+    const RunDev &prun = P.runs[MLP ? P.mlp_run : 0];
+    stage_launch<SMEM, MLP>(P, s_tab, s_run, s_model, s_t0, s_tiles);
+
+    const float4 *tab = SMEM ? s_tab : P.tables;
+    const unsigned FULL = 0xffffffffu;
+    Lane L;
+    bool active = false, done = false;
+    first_units(P, L, active, s_run, s_model);
+
+    for (;;) {
+        if (MLP && __any_sync(FULL, active && L.mlp))
+            mlp2_segment_start(L, active && L.mlp, s_tiles, s_bias, prun);
+
+        for (int g = 0; g < P.groups_per_check; ++g) {
+            // four steps per group (L.n is a multiple of 4 here): Philox blocks n/2, n/2 + 1
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 r = philox4x32_10(make_uint4(((uint32_t)L.n >> 1) + (uint32_t)h, L.traj, L.run_id, 0u),
+                                              P.key_lo, P.key_hi);
+                float z[4];
+                box_muller(r.x, r.y, z[0], z[1]);
+                box_muller(r.z, r.w, z[2], z[3]);
+                if (active && !done) done = em2_step<WEIGHTED, SMEM>(L, z[0], z[1], tab);
+                if (active && !done) done = em2_step<WEIGHTED, SMEM>(L, z[2], z[3], tab);
             }
         }
+        refill_point(P, L, active, done, s_run, s_model);
+        if (!__any_sync(FULL, active)) break;
+        if (P.budget_ns && past_deadline(P, s_t0)) break;
     }
 }
 
 static const void *em_fn(EmVariant v)
 {
+    if (v.rank2) {
+        if (v.mlp) return v.smem ? (const void *)em2_kernel<true, true, true> : (const void *)em2_kernel<true, false, true>;
+        if (v.weighted) return v.smem ? (const void *)em2_kernel<true, true, false> : (const void *)em2_kernel<true, false, false>;
+        return v.smem ? (const void *)em2_kernel<false, true, false> : (const void *)em2_kernel<false, false, false>;
+    }
     if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true, false>
                              : (const void *)em_kernel<true, false, true, true, false>;
     if (v.mlp) return v.smem ? (const void *)em_kernel<true, true, true, false, false>

@@ -12,7 +12,10 @@
 //     with d(-k eta)/dN = -(-k eta) and nu from the exact Eq. (3.13); the
 //     growing mode of Eq. (3.11) gives the 1-D noise of Eq. (3.12):
 //     S = (H/2pi)(2|B|/sqrt(pi)) Gamma(nu)/Gamma(3/2) (sigma/2)^(3/2-nu),
-//     S_pi = (nu - 3/2) S.
+//     S_pi = (nu - 3/2) S;
+//   * numerical matching (Eq. 3.9): the full covariance Xi of
+//     (delta phi_k, delta pi_k) at k = sigma a H and its symmetric square root,
+//     the noise matrix of the full-rank Langevin system, Eq. (2.24).
 //
 // Integrator: adaptive Dormand-Prince 5(4) (Dormand & Prince 1980); the
 // background is stored at every accepted step and evaluated between steps by
@@ -26,6 +29,7 @@
 #include <complex>
 #include <functional>
 #include <limits>
+#include <mutex>
 #include <stdexcept>
 #include <thread>
 #include <vector>
@@ -375,6 +379,34 @@ static double nu_squared(const fpt_model &m, double phi, double pi, int branch)
     return 2.25 - eps1 - 0.5 * eps1 * eps2 * eps2 / (3.0 - eps1) + (eps1 - 3.0) * (d2lnV_term(m) - v1 * v1);
 }
 
+// Run fn(j) for j = 0 .. n-1 on a pool of host threads; the first exception
+// stops the pool and is rethrown.
+static void parallel_points(int n, const std::function<void(int)> &fn)
+{
+    unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::atomic<int> next(0);
+    std::atomic<bool> failed(false);
+    std::string err;
+    std::mutex mu;
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; ++t) {
+        pool.emplace_back([&]() {
+            for (;;) {
+                int j = next.fetch_add(1);
+                if (j >= n || failed.load()) break;
+                try {
+                    fn(j);
+                } catch (const std::exception &e) {
+                    std::lock_guard<std::mutex> g(mu);
+                    if (!failed.exchange(true)) err = e.what();
+                }
+            }
+        });
+    }
+    for (auto &th : pool) th.join();
+    if (failed) throw std::runtime_error(err);
+}
+
 // Bessel-matched noise (S, S_pi) of the mode that crosses sigma a H at
 // background time Ns.
 static void bessel_noise_at_N(const fpt_model &m, const Resolved &r, double Ns, double sigma,
@@ -413,6 +445,37 @@ static void bessel_noise(const fpt_model &m, const Resolved &r, double phi, doub
                          double &S, double &Spi)
 {
     bessel_noise_at_N(m, r, N_of_phi(r.bg, phi, r.bg.N_T, r.bg.N_max()), sigma, S, Spi);
+}
+
+// Full-rank noise of Eq. (3.9) at field value phi: Xi from the full mode
+// (delta phi_k, delta pi_k = d delta phi_k / dN) of k = sigma a H at N_sigma,
+// and S its symmetric square root: for a 2x2 positive semi-definite X with
+// s = sqrt(det X), sqrt(X) = (X + s 1) / sqrt(tr X + 2 s).
+static void numeric_noise(const fpt_model &m, const Resolved &r, double phi, double sigma,
+                          double &Spp, double &Spq, double &Sqq)
+{
+    const Background &bg = r.bg;
+    const double Ns = N_of_phi(bg, phi, bg.N_T, bg.N_max());
+    double ph, pi;
+    int br;
+    bg.state(Ns, ph, pi, br);
+    const double H = hubble(m, ph, pi, br);
+    const double k = sigma * std::exp(Ns) * H;
+    const double N0 = Ns - std::log(kBdRatio / sigma);
+    if (N0 < 0.0) throw std::runtime_error("Bunch-Davies start precedes the background start");
+    std::complex<double> u, du;
+    evolve_mode(m, bg, k, N0, Ns, u, du);
+    // physical mode = u / (exp(N0) sqrt(2k)); power k^3/(2 pi^2) |.|^2
+    const double w = k * k * k / (2.0 * kPi * kPi) / (std::exp(2.0 * N0) * 2.0 * k);
+    const double xpp = w * std::norm(u);
+    const double xpq = w * (u.real() * du.real() + u.imag() * du.imag());
+    const double xqq = w * std::norm(du);
+    const double sd = std::sqrt(std::max(xpp * xqq - xpq * xpq, 0.0));
+    const double den = std::sqrt(xpp + xqq + 2.0 * sd);
+    if (!(den > 0.0)) { Spp = Spq = Sqq = 0.0; return; }
+    Spp = (xpp + sd) / den;
+    Spq = xpq / den;
+    Sqq = (xqq + sd) / den;
 }
 
 // ---------------------------------------------------------------------------
@@ -475,27 +538,30 @@ void build_table(const fpt_model &m, int kind, int n_points, double sigma, doubl
     if (kind != FPT_TABLE_BESSEL && kind != FPT_TABLE_BESSEL_N) throw std::runtime_error("unknown table kind");
     if (!r.has_bg) throw std::runtime_error("Bessel tables need the transition rule (n_in set)");
     if (!(sigma > 0 && sigma <= 10)) throw std::runtime_error("sigma out of (0, 10]");
-    unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
-    std::atomic<int> next(0);
-    std::atomic<bool> failed(false);
-    std::string err;
-    std::vector<std::thread> pool;
-    for (unsigned t = 0; t < nt; ++t) {
-        pool.emplace_back([&]() {
-            for (;;) {
-                int j = next.fetch_add(1);
-                if (j >= n_points || failed.load()) break;
-                try {
-                    if (by_time) bessel_noise_at_N(m, r, r.N_in + lo + h * j, sigma, S[j], Spi[j]);
-                    else bessel_noise(m, r, lo + h * j, sigma, S[j], Spi[j]);
-                } catch (const std::exception &e) {
-                    if (!failed.exchange(true)) err = e.what();
-                }
-            }
-        });
-    }
-    for (auto &th : pool) th.join();
-    if (failed) throw std::runtime_error(err);
+    parallel_points(n_points, [&](int j) {
+        if (by_time) bessel_noise_at_N(m, r, r.N_in + lo + h * j, sigma, S[j], Spi[j]);
+        else bessel_noise(m, r, lo + h * j, sigma, S[j], Spi[j]);
+    });
+}
+
+void build_table2(const fpt_model &m, int kind, int n_points, double sigma, double phi_lo,
+                  double phi_hi, std::vector<double> &Spp, std::vector<double> &Spq,
+                  std::vector<double> &Sqq, double &lo_out, double &h_out)
+{
+    if (kind != FPT_TABLE_NUMERIC) throw std::runtime_error("unknown 2-D table kind");
+    Resolved r = resolve_full(m);
+    if (!r.has_bg) throw std::runtime_error("numerical-matching tables need the transition rule (n_in set)");
+    if (!(sigma > 0 && sigma <= 10)) throw std::runtime_error("sigma out of (0, 10]");
+    double lo = std::isnan(phi_lo) ? r.info.phi_end : phi_lo;
+    double hi = std::isnan(phi_hi) ? r.info.phi_in : phi_hi;
+    if (!(hi > lo)) throw std::runtime_error("need phi_hi > phi_lo");
+    double h = (hi - lo) / (n_points - 1);
+    lo_out = lo;
+    h_out = h;
+    Spp.assign(n_points, 0.0);
+    Spq.assign(n_points, 0.0);
+    Sqq.assign(n_points, 0.0);
+    parallel_points(n_points, [&](int j) { numeric_noise(m, r, lo + h * j, sigma, Spp[j], Spq[j], Sqq[j]); });
 }
 
 }  // namespace fpt_host

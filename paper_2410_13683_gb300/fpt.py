@@ -25,6 +25,7 @@ FPT_OK, FPT_E_INVALID, FPT_E_CUDA, FPT_E_NOMEM, FPT_E_TIMEOUT, FPT_E_STATE = 0, 
 FPT_W_CAPPED = 100
 FPT_POT_PWLINEAR, FPT_POT_EXP = 0, 1
 FPT_TABLE_DESITTER, FPT_TABLE_BESSEL, FPT_TABLE_USER, FPT_TABLE_BESSEL_N, FPT_TABLE_USER_N = 0, 1, 2, 3, 4
+FPT_TABLE_NUMERIC, FPT_TABLE_USER2 = 5, 6
 FPT_BIAS_NONE, FPT_BIAS_CONST, FPT_BIAS_MLP = 0, 1, 2
 FPT_TRAJ_PASSED, FPT_TRAJ_CAPPED, FPT_TRAJ_ABORTED = 0, 1, 2
 FPT_MLP_LOG_X = 1
@@ -57,7 +58,7 @@ class fpt_run_desc(C.Structure):
                 ("n_traj", C.c_int64), ("traj_offset", C.c_int64), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("mlp_segment", C.c_int32), ("mlp", C.c_void_p),
                 ("mlp_shift", C.c_float * 3), ("mlp_scale", C.c_float * 3),
-                ("alpha_max", C.c_float), ("mlp_flags", C.c_int32)]
+                ("alpha_max", C.c_float), ("mlp_flags", C.c_int32), ("A2", C.c_double)]
 
 
 class fpt_traj_out(C.Structure):
@@ -102,7 +103,11 @@ _SIGNATURES = {
     "fpt_noise_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                   C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
+    "fpt_noise_table2": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                   C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "fpt_resolve_model": (C.c_int, [C.POINTER(fpt_model), C.POINTER(fpt_model_info)]),
+    "fpt_table_build2": (C.c_int, [C.POINTER(fpt_model), C.c_int32, C.c_int32, C.c_double,
+                                   C.c_double, C.c_double, C.c_void_p]),
     "fpt_table_build": (C.c_int, [C.POINTER(fpt_model), C.c_int32, C.c_int32, C.c_double,
                                   C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "fpt_set_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
@@ -291,6 +296,29 @@ def fpt_noise_table(ctx: Context, model: int, kind: int, n_points: int, sigma: f
     return S, T
 
 
+def fpt_table_build2(model, kind: int, n_points: int, sigma: float = 1.0, phi_lo: float = NAN,
+                     phi_hi: float = NAN):
+    """Full-rank table planes (S_phiphi, S_phipi, S_pipi), each n_points."""
+    out = np.zeros(3 * n_points)
+    m = model_struct(model)
+    _check(load().fpt_table_build2(C.byref(m), kind, n_points, sigma, phi_lo, phi_hi, _ptr(out)))
+    return out[:n_points], out[n_points:2 * n_points], out[2 * n_points:]
+
+
+def fpt_noise_table2(ctx: Context, model: int, kind: int, n_points: int, sigma: float = 1.0,
+                     phi_lo: float = NAN, phi_hi: float = NAN, user_S=None):
+    """Full-rank (2-D) noise table; user_S = (S_phiphi, S_phipi, S_pipi) for USER2."""
+    out = np.zeros(3 * n_points)
+    uS = None
+    if kind == FPT_TABLE_USER2:
+        uS = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=np.float64) for v in user_S]))
+        if uS.shape != (3 * n_points,):
+            raise ValueError("user tables must have 3 planes of n_points entries")
+    _check(load().fpt_noise_table2(ctx.handle, model, kind, n_points, sigma, phi_lo, phi_hi,
+                                   _ptr(uS), _ptr(out)), ctx.handle)
+    return out[:n_points], out[n_points:2 * n_points], out[2 * n_points:]
+
+
 def fpt_set_launch(ctx: Context, block: int = 0, blocks_per_sm: int = 0, check_steps: int = 0,
                    use_graph: bool = True, deadline_s: float = 0.0):
     l = fpt_launch(block=block, blocks_per_sm=blocks_per_sm, check_steps=check_steps,
@@ -316,10 +344,11 @@ def fpt_autotune(ctx: Context, runs: Sequence[fpt_run_desc], fraction: float = 0
 def run_desc(model: int = 0, n_traj: int = 0, seed: int = 0, run_id: int = 0, A: float = 0.0,
              traj_offset: int = 0, bias_kind: Optional[int] = None, mlp=None, mlp_segment: int = 0,
              mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max: float = 0.0,
-             mlp_flags: int = 0):
+             mlp_flags: int = 0, A2: float = 0.0):
     if bias_kind is None:
-        bias_kind = FPT_BIAS_MLP if mlp is not None else (FPT_BIAS_CONST if A != 0.0 else FPT_BIAS_NONE)
-    return fpt_run_desc(model=model, bias_kind=bias_kind, A=A, n_traj=n_traj,
+        bias_kind = FPT_BIAS_MLP if mlp is not None else (
+            FPT_BIAS_CONST if (A != 0.0 or A2 != 0.0) else FPT_BIAS_NONE)
+    return fpt_run_desc(model=model, bias_kind=bias_kind, A=A, A2=A2, n_traj=n_traj,
                         traj_offset=traj_offset, seed=seed, run_id=run_id,
                         mlp_segment=mlp_segment, mlp=_ptr(mlp),
                         mlp_shift=(C.c_float * 3)(*mlp_shift), mlp_scale=(C.c_float * 3)(*mlp_scale),

@@ -147,3 +147,27 @@ def test_time_indexed_bessel_table_matches_oracle():
 def test_time_indexed_table_needs_a_window():
     with pytest.raises(fpt.FptError):
         fpt.fpt_table_build(W.USR_MODEL, fpt.FPT_TABLE_BESSEL_N, 64, 1.0)
+
+
+@pytest.mark.parametrize("sigma,rtol", [(1.0, 1e-7), (0.1, 1e-5)])
+def test_numeric_table_matches_oracle(sigma, rtol):
+    """Full-rank table (Eq. 3.9, symmetric square root) of the host builder vs
+    the oracle's numerical matching; at sigma = 0.1 Xi is squeezed
+    (det / (Xi_pp Xi_qq) ~ 1e-5), so sqrt(det) carries the cancellation of
+    the determinant and the tolerance is wider."""
+    m = W.USR_MODEL
+    M = 1024
+    Spp, Spq, Sqq = fpt.fpt_table_build2(m, fpt.FPT_TABLE_NUMERIC, M, sigma)
+    idx = [0, 1, 100, 511, 1000, 1023]
+    tab = T.numeric_table(m, T.resolve(m), M, sigma, indices=idx)
+    for got, ref in ((Spp, tab.Spp), (Spq, tab.Spq), (Sqq, tab.Sqq)):
+        np.testing.assert_allclose(got[idx], ref[idx], rtol=rtol)
+
+
+def test_numeric_table_arguments():
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_table_build2(W.LINEAR.model, fpt.FPT_TABLE_NUMERIC, 16, 1.0)   # no transition rule
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_table_build2(W.USR_MODEL, fpt.FPT_TABLE_USER2, 16, 1.0)       # user tables are not built
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_table_build2(W.USR_MODEL, fpt.FPT_TABLE_NUMERIC, 16, 0.0)
