@@ -39,14 +39,16 @@ def usr_numeric():
 def test_2d_usr_parity(torch, usr_numeric, betas):
     """Sudden-transition model with the numerically matched full-rank noise
     (sigma = 1): direct and two constant standardised biases in one launch;
-    5000 trajectories per run (a ragged tail of the 32-lane refill)."""
+    5000 trajectories per run (a ragged tail of the 32-lane refill); capped
+    paths carry the CAPPED status on both sides."""
     m, res, tab = usr_numeric
     n = 5000
     with fpt.fpt_init_model([m]) as ctx:
         _upload2(ctx, tab)
         runs = [fpt.run_desc(0, n, seed=80, run_id=r, A=b1, A2=b2) for r, (b1, b2) in enumerate(betas)]
         st, g = gpu_run(ctx, runs, [n] * len(runs))
-        assert st == fpt.FPT_OK
+        # the bias (0.5, -0.3) holds ~10% of the paths above phi_end until the step cap
+        assert st in (fpt.FPT_OK, fpt.FPT_W_CAPPED)
     for r, (b1, b2) in enumerate(betas):
         o = OS.run2(m, res, tab, seed=80, run_id=r, n=n, A=b1, A2=b2)
         o.phi_end_value = res.phi_end
