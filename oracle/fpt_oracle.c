@@ -96,11 +96,13 @@ void oracle_normals4(uint64_t seed, uint32_t run_id, uint32_t traj,
 /* Model, table and bias descriptions.                                      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int32_t kind;        /* 0: piecewise-linear, relative slopes; 1: V0 exp(mu phi) */
+    int32_t kind;        /* 0: piecewise-linear, relative slopes; 1: V0 exp(mu phi);
+                            2: Gaussian bump V0 phi^2/(m^2+phi^2) [1 + K exp(-(phi-phi0)^2/(2 w^2))] */
     int32_t pad;
     double V0, a_plus, a_minus, phi_star, mu;
     double phi_in, pi_in, phi_end, dN;
     int64_t max_steps;
+    double bump_K, bump_m, bump_w, bump_phi0;
 } oracle_model;
 
 typedef struct {
@@ -125,11 +127,19 @@ typedef struct {
     double in_shift[3], in_scale[3];             /* input = (s - shift) * scale */
 } oracle_bias;
 
-/* Slope term V'(phi)/V(phi) of the two potential families. */
+/* Slope term V'(phi)/V(phi) of the potential families. The Gaussian bump of
+ * Sec. 4.3, V = V0 f (1 + g) with f = phi^2/(m^2 + phi^2) and
+ * g = K exp(-(phi - phi0)^2/(2 w^2)), has V'/V = f'/f + g'/(1 + g),
+ * f'/f = 2 m^2 / (phi (m^2 + phi^2)), g' = -g (phi - phi0)/w^2. */
 static double dlnV(const oracle_model *m, double phi)
 {
     if (m->kind == 1)
         return m->mu;
+    if (m->kind == 2) {
+        double m2 = m->bump_m * m->bump_m, d = phi - m->bump_phi0, w2 = m->bump_w * m->bump_w;
+        double g = m->bump_K * exp(-0.5 * d * d / w2);
+        return 2.0 * m2 / (phi * (m2 + phi * phi)) - g * d / (w2 * (1.0 + g));
+    }
     double d = phi - m->phi_star;
     double a = (phi >= m->phi_star) ? m->a_plus : m->a_minus;
     return a / (1.0 + a * d);

@@ -32,7 +32,9 @@ class _Model(C.Structure):
                 ("V0", C.c_double), ("a_plus", C.c_double), ("a_minus", C.c_double),
                 ("phi_star", C.c_double), ("mu", C.c_double),
                 ("phi_in", C.c_double), ("pi_in", C.c_double), ("phi_end", C.c_double),
-                ("dN", C.c_double), ("max_steps", C.c_int64)]
+                ("dN", C.c_double), ("max_steps", C.c_int64),
+                ("bump_K", C.c_double), ("bump_m", C.c_double), ("bump_w", C.c_double),
+                ("bump_phi0", C.c_double)]
 
 
 class _Table(C.Structure):
@@ -135,7 +137,9 @@ class Trajectories:
 def model_struct(m, phi_in, pi_in, phi_end) -> _Model:
     return _Model(kind=m.kind, pad=0, V0=m.V0, a_plus=m.a_plus, a_minus=m.a_minus,
                   phi_star=m.phi_star, mu=m.mu, phi_in=phi_in, pi_in=pi_in,
-                  phi_end=phi_end, dN=m.dN, max_steps=m.max_steps)
+                  phi_end=phi_end, dN=m.dN, max_steps=m.max_steps,
+                  bump_K=getattr(m, "bump_K", 0.0), bump_m=getattr(m, "bump_m", 0.0),
+                  bump_w=getattr(m, "bump_width", 0.0), bump_phi0=getattr(m, "bump_phi0", 0.0))
 
 
 class MLPBias:

@@ -43,18 +43,48 @@ BD_RATIO = 100.0       # k / (aH) at the Bunch-Davies start, times sigma
 # --------------------------------------------------------------------------
 # Potential (Eq. 4.11 with relative slopes; exponential test model)
 # --------------------------------------------------------------------------
+def _bump_parts(m, phi):
+    """Gaussian bump (Sec. 4.3): V = V0 f (1 + g), f = phi^2/(m^2 + phi^2),
+    g = K exp(-(phi - phi0)^2/(2 w^2)). Returns f'/f, f''/f, g, g', g''."""
+    m2, w2 = m.bump_m ** 2, m.bump_width ** 2
+    d = phi - m.bump_phi0
+    g = m.bump_K * math.exp(-0.5 * d * d / w2)
+    q = m2 + phi * phi
+    f1 = 2.0 * m2 / (phi * q)
+    f2 = 2.0 * m2 * (m2 - 3.0 * phi * phi) / (phi * phi * q * q)
+    g1 = -g * d / w2
+    g2 = g * (d * d / w2 - 1.0) / w2
+    return f1, f2, g, g1, g2
+
+
 def dlnV(m, phi: float, branch: int | None = None) -> float:
     """V'/V. ``branch`` = +1/-1 forces the side of the kink."""
     if m.kind == 1:
         return m.mu
+    if m.kind == 2:
+        f1, _, g, g1, _ = _bump_parts(m, phi)
+        return f1 + g1 / (1.0 + g)
     above = (phi >= m.phi_star) if branch is None else (branch > 0)
     a = m.a_plus if above else m.a_minus
     return a / (1.0 + a * (phi - m.phi_star))
 
 
+def d2V_over_V(m, phi: float, branch: int | None = None) -> float:
+    """V''/V away from the kink (zero for the piecewise-linear potential)."""
+    if m.kind == 1:
+        return m.mu * m.mu
+    if m.kind == 2:
+        f1, f2, g, g1, g2 = _bump_parts(m, phi)
+        return f2 + 2.0 * f1 * g1 / (1.0 + g) + g2 / (1.0 + g)
+    return 0.0
+
+
 def V_of(m, phi: float, branch: int | None = None) -> float:
     if m.kind == 1:
         return m.V0 * math.exp(m.mu * phi)
+    if m.kind == 2:
+        _, _, g, _, _ = _bump_parts(m, phi)
+        return m.V0 * phi * phi / (m.bump_m ** 2 + phi * phi) * (1.0 + g)
     above = (phi >= m.phi_star) if branch is None else (branch > 0)
     a = m.a_plus if above else m.a_minus
     return m.V0 * (1.0 + a * (phi - m.phi_star))
@@ -71,14 +101,15 @@ def hubble(m, phi, pi, branch=None):
 @dataclass
 class Background:
     model: object
-    N_T: float                 # transition time (phi = phi_star); nan if none
+    N_T: float                 # transition time (kink crossing, or USR onset); nan if none
     pre: object                # OdeSolution for N <= N_T (branch +)
     post: object               # OdeSolution for N >= N_T (branch -)
     N_max: float
+    kink: bool = True          # False: smooth potential, N_T only marks the USR onset
 
     def state(self, N: float):
         sol, br = (self.pre, +1) if (not math.isnan(self.N_T) and N < self.N_T) else (self.post, -1)
-        if math.isnan(self.N_T):
+        if math.isnan(self.N_T) or not self.kink:
             br = None
         y = sol(N)
         return float(y[0]), float(y[1]), br
@@ -91,9 +122,30 @@ def _bg_rhs(branch):
     return f
 
 
+def _eps2(m, phi, pi):
+    dpi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi))
+    return 2.0 * dpi / pi
+
+
 def solve_background(m, phi0: float, N_max: float) -> Background:
-    """Background from phi0 on the slow-roll attractor pi0 = -V'/V(phi0)."""
+    """Background from phi0 on the slow-roll attractor pi0 = -V'/V(phi0).
+
+    Piecewise-linear potential: N_T is the kink crossing phi = phi_star.
+    Gaussian bump: N_T is the onset of ultra-slow roll, the first time
+    eps2 = 2 pi'/pi falls to -3 (Sec. 4.3); the background then continues
+    smoothly to N_T + N_max."""
     pi0 = -dlnV(m, phi0)
+    if m.kind == 2:
+        ev = lambda N, y, m: _eps2(m, y[0], y[1]) + 3.0
+        ev.terminal, ev.direction = True, -1
+        s1 = integrate.solve_ivp(_bg_rhs(None), (0.0, 200.0), [phi0, pi0], method="DOP853",
+                                 rtol=RTOL_BG, atol=ATOL_BG, dense_output=True, events=ev, args=(m,))
+        if s1.status != 1:
+            raise ValueError("the background never enters ultra-slow roll (eps2 > -3 throughout)")
+        N_T = float(s1.t_events[0][0])
+        s2 = integrate.solve_ivp(_bg_rhs(None), (N_T, N_T + N_max), s1.y_events[0][0], method="DOP853",
+                                 rtol=RTOL_BG, atol=ATOL_BG, dense_output=True, args=(m,))
+        return Background(m, N_T, s1.sol, s2.sol, N_T + N_max, kink=False)
     if m.kind == 0 and phi0 > m.phi_star:
         ev = lambda N, y, m: y[0] - m.phi_star
         ev.terminal, ev.direction = True, -1
@@ -134,7 +186,8 @@ def resolve(m) -> Resolved:
     n_end e-folds after N_T.
     """
     if not math.isnan(m.n_in):
-        bg = solve_background(m, m.bg_phi0, N_max=max(60.0, 2 * m.n_end + 40.0))
+        span = (m.n_end + 10.0) if m.kind == 2 else max(60.0, 2 * m.n_end + 40.0)
+        bg = solve_background(m, m.bg_phi0, N_max=span)
         N_in = bg.N_T + m.n_in
         N_end = bg.N_T + m.n_end
         phi_in, pi_in, _ = bg.state(N_in)
@@ -163,11 +216,11 @@ def flow(m, phi, pi, branch):
 
 
 def nu_squared(m, phi, pi, branch) -> float:
-    """Exact nu^2 of Eq. (3.13); V'' = 0 away from the kink for both models
-    except the exponential one (V''/V = mu^2)."""
+    """Exact nu^2 of Eq. (3.13) with V''/V of the model (zero away from the
+    kink of the piecewise-linear potential)."""
     eps1, eps2, H, _ = flow(m, phi, pi, branch)
     v1 = dlnV(m, phi, branch)
-    v2 = (m.mu * m.mu) if m.kind == 1 else 0.0
+    v2 = d2V_over_V(m, phi, branch)
     return 2.25 - eps1 - 0.5 * eps1 * eps2 * eps2 / (3.0 - eps1) + (eps1 - 3.0) * (v2 - v1 * v1)
 
 
@@ -181,7 +234,7 @@ def _mode_rhs(N, y, m, k, branch):
     H2 = V / (3.0 - 0.5 * pi * pi)
     eps1 = 0.5 * pi * pi
     dpi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi, branch))
-    v2 = (m.mu * m.mu) if m.kind == 1 else 0.0          # V''/V
+    v2 = d2V_over_V(m, phi, branch)                     # V''/V
     mass = (k * k) / (math.exp(2.0 * N) * H2) + v2 * V / H2 - (3.0 - eps1) * pi * pi - 2.0 * pi * dpi
     return [pi, dpi,
             urp, -(3.0 - eps1) * urp - mass * ur,
@@ -196,7 +249,9 @@ def evolve_mode(m, bg: Background, k: float, N0: float, N1: float, u0: complex,
     Returns (u, du/dN, final state vector)."""
     phi0, pi0, br0 = bg.state(N0)
     y = [phi0, pi0, u0.real, du0.real, u0.imag, du0.imag]
-    if not math.isnan(bg.N_T) and N0 < bg.N_T < N1:
+    if not bg.kink or math.isnan(bg.N_T):
+        segments = [(N0, N1, None)]
+    elif N0 < bg.N_T < N1:
         segments = [(N0, bg.N_T, +1), (bg.N_T, N1, -1)]
     elif not math.isnan(bg.N_T):
         segments = [(N0, N1, +1 if N0 < bg.N_T else -1)]

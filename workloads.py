@@ -16,6 +16,10 @@ Model conventions (all workloads):
   * the exponential potential V = V0 exp(mu phi) is a test model whose
     attractor pi = -mu is exact, so the dynamics reduce to a Gaussian random
     walk (used to pin the sampler against first-passage closed forms);
+  * the Gaussian-bump potential (Sec. 4.3),
+        V(phi) = V0 phi^2/(m^2 + phi^2) [1 + K exp(-(phi - phi0)^2 / (2 width^2))],
+    with the paper's K, m, width and phi0; V0 is not printed and is fixed by
+    normalising the peak of the linear power spectrum;
   * e-fold step dN = 1e-3 throughout (the paper prints no step size).
 """
 from __future__ import annotations
@@ -29,6 +33,7 @@ import numpy as np
 # Potential kinds (mirrors FPT_POT_* in include/fpt.h; values are plain ints).
 POT_PWLINEAR = 0
 POT_EXP = 1
+POT_BUMP = 2
 
 # Noise-table kinds (mirrors FPT_TABLE_*).
 TABLE_DESITTER = 0
@@ -70,6 +75,11 @@ class Model:
     n_end: float = NAN
     dN: float = 1e-3
     max_steps: int = 1 << 20
+    # POT_BUMP: V0 phi^2/(m^2 + phi^2) [1 + K exp(-(phi - phi0)^2 / (2 width^2))]
+    bump_K: float = 0.0
+    bump_m: float = 0.0
+    bump_width: float = 0.0
+    bump_phi0: float = 0.0
 
 
 @dataclass(frozen=True)
@@ -132,6 +142,18 @@ USR_LEARNED = Workload(
 )
 LEARNED_ROUNDS = 20
 LEARNED_TRAIN_TRAJ = 1 << 20
+
+# --- Gaussian bump (Sec. 4.3): smooth transition to ultra-slow roll ---------
+# K, m, width, phi0 as printed; V0 (not printed) makes the linear power
+# spectrum peak at 5e-3 (tests/golden/make_bump_v0.py -> bump_v0.json).
+# The background starts at phi = 2.6 on the attractor; N_T is the onset of
+# ultra-slow roll (eps2 = -3). The simulated modes start half-way through the
+# ultra-slow-roll phase (which lasts 2.4 e-folds) and span 4 e-folds.
+BUMP_V0 = 7.76487e-11
+BUMP_MODEL = Model(kind=POT_BUMP, V0=BUMP_V0, bump_K=1.17e-3, bump_m=0.5,
+                   bump_width=1.59e-2, bump_phi0=2.18812, bg_phi0=2.6,
+                   n_in=1.2, n_end=5.2, dN=1e-3, max_steps=1 << 18)
+BUMP_TABLE = Table(kind=TABLE_BESSEL, n_points=4096, sigma=1.0)
 
 # --- exponential test model: exact Gaussian random walk ---------------------
 # V = V0 exp(mu phi) has V'/V = mu, so pi = -mu is an exact fixed point of the
