@@ -55,7 +55,12 @@ enum {
      * (phi_star = 0). */
     FPT_POT_PWLINEAR = 0,
     /* V = V0 exp(mu phi): V'/V = mu, exact attractor pi = -mu (test model). */
-    FPT_POT_EXP = 1
+    FPT_POT_EXP = 1,
+    /* Gaussian bump, Eq. (4.12):
+     * V = V0 phi^2/(bump_m^2 + phi^2) [1 + bump_K exp(-(phi - bump_phi0)^2 / (2 bump_width^2))].
+     * With the transition rule, N_T is the onset of ultra-slow roll (the
+     * first time eps2 = 2 pi'/pi reaches -3 on the background). */
+    FPT_POT_BUMP = 2
 };
 
 /* Noise-table kinds (fpt_noise_table). */
@@ -98,9 +103,10 @@ enum { FPT_TRAJ_PASSED = 0, FPT_TRAJ_CAPPED = 1, FPT_TRAJ_ABORTED = 2 };
  * the attractor value -V'/V(phi_in)), or -- when n_in is not NaN -- resolved
  * from the classical background (Eq. 2.21 without noise) that starts at
  * bg_phi0 on the slow-roll attractor: phi_in, pi_in are the background values
- * n_in e-folds after the transition time N_T (phi = phi_star) and phi_end the
- * background field n_end e-folds after N_T (the paper starts after the
- * transition and sets the start/end by the mode range, Secs. 4.1-4.2).
+ * n_in e-folds after the transition time N_T (phi = phi_star; for the bump
+ * the onset of ultra-slow roll) and phi_end the background field n_end
+ * e-folds after N_T (the paper starts after the transition and sets the
+ * start/end by the mode range, Secs. 4.1-4.3).
  * Passage is the first step n >= 1 with phi_n <= phi_end; N = n dN.
  */
 typedef struct {
@@ -119,6 +125,10 @@ typedef struct {
     double n_end;          /* transition rule: end, e-folds after N_T        */
     double dN;             /* e-fold step (> 0)                              */
     int64_t max_steps;     /* step cap per trajectory (>= 1, < 2^31)         */
+    double bump_K;         /* FPT_POT_BUMP: bump height                      */
+    double bump_m;         /* FPT_POT_BUMP: mass scale of the plateau        */
+    double bump_width;     /* FPT_POT_BUMP: Gaussian width (> 0)             */
+    double bump_phi0;      /* FPT_POT_BUMP: bump position                    */
 } fpt_model;
 
 /* Resolved start/end of a model (FP64, from the background solve). */

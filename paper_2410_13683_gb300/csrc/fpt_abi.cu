@@ -58,6 +58,7 @@ struct fpt_ctx {
     float4 *d_tables = nullptr;
     size_t tables_cap = 0;
     std::vector<int> table_offset;
+    std::vector<int> region_entries;   // float4 entries per model: noise table (+ drift table)
     RunDev *d_runs = nullptr;
     RunDev *h_runs = nullptr;           // pinned staging
     unsigned long long *d_cursor = nullptr;
@@ -404,6 +405,7 @@ fpt_status fpt_init_model(fpt_ctx **pctx, const fpt_model *models, int32_t n_mod
     ctx->infos = infos;
     ctx->tables.resize(n_models);
     ctx->table_offset.assign(n_models, 0);
+    ctx->region_entries.assign(n_models, 0);
     auto bail = [&](cudaError_t err, const char *what) {
         fpt_status s = (err == cudaErrorMemoryAllocation) ? FPT_E_NOMEM : FPT_E_CUDA;
         fail(nullptr, s, std::string(what) + ": " + cudaGetErrorString(err));
@@ -443,12 +445,46 @@ fpt_status fpt_model_get_info(const fpt_ctx *ctx, int32_t model, fpt_model_info 
 // Re-pack every ready table into one float4 array and refresh the model
 // descriptors: entry j of a model = (S_j, S_{j+1} - S_j, T_j, T_{j+1} - T_j)
 // times sqrt(dN), in FP32.
+// Cubic table of V'/V for the Gaussian bump (see drift_vpv in fpt_kernels.cu):
+// kDriftIntervals intervals over x = phi - phi_end in [0, X], X = 16 (phi_in -
+// phi_end), capped at the background start; Hermite coefficients from the FP64
+// values v and slopes v' = V''/V - (V'/V)^2 at the nodes.
+static const int kDriftIntervals = 1024;
+
+static double drift_top(const fpt_model &m, const fpt_model_info &inf)
+{
+    double X = 16.0 * (inf.phi_in - inf.phi_end);
+    if (!std::isnan(m.n_in)) X = std::min(X, m.bg_phi0 - inf.phi_end);
+    return X;
+}
+
+static void drift_table(const fpt_model &m, const fpt_model_info &inf, float4 *out)
+{
+    const double X = drift_top(m, inf), h = X / kDriftIntervals;
+    std::vector<double> v(kDriftIntervals + 1), dv(kDriftIntervals + 1);
+    for (int j = 0; j <= kDriftIntervals; ++j) {
+        const double phi = inf.phi_end + h * j;
+        v[j] = fpt_host::dlnV(m, phi, 0);
+        dv[j] = fpt_host::d2V_over_V(m, phi) - v[j] * v[j];
+    }
+    for (int j = 0; j < kDriftIntervals; ++j) {
+        const double v0 = v[j], v1 = v[j + 1], d0 = h * dv[j], d1 = h * dv[j + 1];
+        out[j] = make_float4((float)v0, (float)d0, (float)(3.0 * (v1 - v0) - 2.0 * d0 - d1),
+                             (float)(2.0 * (v0 - v1) + d0 + d1));
+    }
+    out[kDriftIntervals] = make_float4((float)v[kDriftIntervals], 0.0f, 0.0f, 0.0f);
+}
+
 static fpt_status upload_tables(fpt_ctx *ctx)
 {
     size_t total = 0;
     for (size_t i = 0; i < ctx->tables.size(); ++i) {
         ctx->table_offset[i] = (int)total;
-        if (ctx->tables[i].ready) total += ctx->tables[i].entries();
+        int e = 0;
+        if (ctx->tables[i].ready)
+            e = ctx->tables[i].entries() + (ctx->models[i].kind == FPT_POT_BUMP ? kDriftIntervals + 1 : 0);
+        ctx->region_entries[i] = e;
+        total += e;
     }
     std::vector<float4> packed(std::max<size_t>(total, 1));
     std::vector<ModelDev> md(ctx->models.size());
@@ -471,6 +507,18 @@ static fpt_status upload_tables(fpt_ctx *ctx)
         }
         d.x_in = (float)(inf.phi_in - inf.phi_end);
         d.pi_in = (float)inf.pi_in;
+        d.dtab = -1;
+        if (m.kind == FPT_POT_BUMP && t.ready) {
+            d.dtab = t.entries();
+            d.d_scale = (float)(kDriftIntervals / drift_top(m, inf));
+            d.d_umax = (float)kDriftIntervals;
+            d.bump_m2 = (float)(m.bump_m * m.bump_m);
+            d.bump_phi_end = (float)inf.phi_end;
+            d.bump_dphi0 = (float)(inf.phi_end - m.bump_phi0);
+            d.bump_inv_w2 = (float)(1.0 / (m.bump_width * m.bump_width));
+            d.bump_K = (float)m.bump_K;
+            drift_table(m, inf, &packed[ctx->table_offset[i] + t.entries()]);
+        }
         d.dN = (float)m.dN;
         d.max_steps = (int32_t)m.max_steps;
         d.table_offset = ctx->table_offset[i];
@@ -638,6 +686,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     bool weighted = false;
     bool nidx = false;
     int rank2 = -1;
+    int bump = -1;
     int mlp_run = -1;
     for (int r = 0; r < n_runs; ++r) {
         const fpt_run_desc &d = runs[r];
@@ -667,6 +716,12 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
         if (d.bias_kind == FPT_BIAS_CONST && (!std::isfinite(d.A) || !std::isfinite(d.A2)))
             return fail(ctx, FPT_E_INVALID, "A and A2 must be finite");
         if (d.n_traj > 0) {
+            const bool bp = ctx->models[d.model].kind == FPT_POT_BUMP;
+            if (bump < 0) bump = bp ? 1 : 0;
+            else if (bump != (bp ? 1 : 0))
+                return fail(ctx, FPT_E_INVALID, "runs of one call must all use the bump potential or none");
+            if (bp && ctx->tables[d.model].n_indexed)
+                return fail(ctx, FPT_E_INVALID, "the bump potential needs a phi-indexed noise table");
             const bool r2 = ctx->tables[d.model].rank2;
             if (rank2 < 0) rank2 = r2 ? 1 : 0;
             else if (rank2 != (r2 ? 1 : 0))
@@ -731,8 +786,8 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const bool mlp = mlp_run >= 0;
     if (mlp && ctx->record_mode && rank2 == 1)
         return fail(ctx, FPT_E_INVALID, "training records need a 1-D noise table");
-    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1};
-    const size_t smem_bytes = (smem ? sizeof(float4) * ctx->tables[smem_model].entries() : 0) +
+    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
+    const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
     // the learned-proposal stepper is compiled for at most kMlpMaxBlock threads
     const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
@@ -751,7 +806,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     p.n_runs = n_runs;
     p.tables = ctx->d_tables;
     p.smem_table_offset = smem ? ctx->table_offset[smem_model] : 0;
-    p.smem_table_points = smem ? ctx->tables[smem_model].entries() : 0;
+    p.smem_table_points = smem ? ctx->region_entries[smem_model] : 0;
     p.total_units = total;
     p.cursor = ctx->d_cursor;
     p.flags = ctx->d_flags;
@@ -774,7 +829,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             GraphKey key{weighted, smem, grid, block, smem_bytes, p.groups_per_check, n_runs,
                          smem ? smem_model : -1, total,
                          (mlp ? 1 : 0) + (var.rec ? 2 : 0) + (var.nidx ? 4 : 0) + (var.rank2 ? 8 : 0) +
-                             16 * p.mlp_run};
+                             (var.dtab ? 16 : 0) + 32 * p.mlp_run};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 cudaGraph_t g;

@@ -22,6 +22,7 @@ void build_table2(const fpt_model &m, int kind, int n_points, double sigma, doub
                   double phi_hi, std::vector<double> &Spp, std::vector<double> &Spq,
                   std::vector<double> &Sqq, double &lo_out, double &h_out);
 double dlnV(const fpt_model &m, double phi, int branch);
+double d2V_over_V(const fpt_model &m, double phi);
 double Vof(const fpt_model &m, double phi, int branch);
 double hubble(const fpt_model &m, double phi, double pi, int branch);
 }  // namespace fpt_host
@@ -50,6 +51,12 @@ struct ModelDev {
     int32_t table_offset;      // first float4 entry of this model's table
     int32_t nidx;              // 1: table indexed by the step count (noise window)
     int32_t rank2;             // 1: full-rank 2-D noise table (M + 1 entries)
+    // Gaussian bump: cubic V'/V table after the noise entries (dtab >= 0) and
+    // the closed form's constants for fields above it
+    int32_t dtab;              // first drift entry, relative to the model's table; -1: none
+    float d_scale;             // drift-table coordinate u = x * d_scale
+    float d_umax;              // intervals of the drift table
+    float bump_m2, bump_phi_end, bump_dphi0, bump_inv_w2, bump_K;
     int32_t win_lo, win_hi;    // noise window [win_lo, win_hi] in steps (nidx)
 };
 
@@ -125,6 +132,7 @@ enum {
 struct EmVariant {
     bool weighted, smem, mlp, rec, nidx;
     bool rank2;              // full-rank 2-D noise stepper
+    bool dtab;               // V'/V from the bump's cubic table
 };
 
 // Host wrappers implemented in fpt_kernels.cu.

@@ -103,7 +103,10 @@ struct Lane {                // per-thread trajectory state and its constants
     uint32_t traj, run_id;
     float cb, half_cb2, dN, sqrt_dN;
     float cb_b;              // 2-D noise: beta_2 sqrt(dN) (cb = beta_1 sqrt(dN))
-    float x_star, a_plus, a_minus, b_plus, b_minus;
+    union {                  // drift constants of the lane's potential
+        struct { float x_star, a_plus, a_minus, b_plus, b_minus; } pw;   // piecewise-linear / exponential
+        struct { float scale, umax; int dtab, model; } bump;              // Gaussian bump: cubic V'/V table
+    } dc;
     float u_scale, u_shift, u_max;
     int tbase;
     bool mlp;
@@ -138,11 +141,18 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.mlp = r.is_mlp != 0;
     L.dN = m.dN;
     L.sqrt_dN = r.sqrt_dN;
-    L.x_star = m.x_star;
-    L.a_plus = m.a_plus;
-    L.a_minus = m.a_minus;
-    L.b_plus = m.b_plus;
-    L.b_minus = m.b_minus;
+    if (m.dtab >= 0) {
+        L.dc.bump.scale = m.d_scale;
+        L.dc.bump.umax = m.d_umax;
+        L.dc.bump.dtab = m.dtab;
+        L.dc.bump.model = r.model;
+    } else {
+        L.dc.pw.x_star = m.x_star;
+        L.dc.pw.a_plus = m.a_plus;
+        L.dc.pw.a_minus = m.a_minus;
+        L.dc.pw.b_plus = m.b_plus;
+        L.dc.pw.b_minus = m.b_minus;
+    }
     L.u_scale = m.u_scale;
     L.u_shift = m.u_shift;
     L.u_max = (float)(m.M - 1);
@@ -178,13 +188,49 @@ __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restri
     return SMEM ? tab[i] : __ldg(tab + L.tbase + i);
 }
 
+// V'/V at the lane's field. Piecewise-linear (relative slopes) and
+// exponential potentials: a / (1 + b (x - x_star)), branch by side.
+// Gaussian bump (DTAB): near its inflection point V'/V is the small
+// difference of two terms of size ~0.05, which FP32 cannot resolve, so it is
+// read from a cubic (Hermite) table of the FP64 values on a uniform x grid
+// (coefficients c0..c3 of s in [0, 1] per interval; one padding entry), and
+// evaluated from the closed form in FP32 only above the table.
+template <bool DTAB, bool SMEM>
+__device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restrict__ tab,
+                                           const ModelDev *s_model)
+{
+    if (!DTAB) {
+        const float d = L.x - L.dc.pw.x_star;
+        const bool up = d >= 0.0f;
+        const float a = up ? L.dc.pw.a_plus : L.dc.pw.a_minus;
+        const float b = up ? L.dc.pw.b_plus : L.dc.pw.b_minus;
+        return __fdividef(a, fmaf(b, d, 1.0f));
+    }
+    const float u = fmaxf(L.x * L.dc.bump.scale, 0.0f);
+    if (u <= L.dc.bump.umax) {
+        const float kMagic = 12582912.0f;                    // 1.5 * 2^23
+        const float t = (u - 0.5f) + kMagic;
+        const int i = __float_as_int(t) - 0x4b400000;
+        const float sv = u - (t - kMagic);
+        const float4 c = SMEM ? tab[L.dc.bump.dtab + i] : __ldg(tab + L.tbase + L.dc.bump.dtab + i);
+        return fmaf(sv, fmaf(sv, fmaf(sv, c.w, c.z), c.y), c.x);
+    }
+    const ModelDev &md = s_model[L.dc.bump.model];
+    const float phi = L.x + md.bump_phi_end;
+    const float d = L.x + md.bump_dphi0;                     // phi - phi0
+    const float g = md.bump_K * __expf(-0.5f * d * d * md.bump_inv_w2);
+    return __fdividef(2.0f * md.bump_m2, phi * fmaf(phi, phi, md.bump_m2)) -
+           __fdividef(g * d * md.bump_inv_w2, 1.0f + g);
+}
+
 // One Euler-Maruyama step of Eq. (4.7) with bias amplitude L.cb / sqrt(dN).
 // The field increment (drift + bias + noise) is formed first and added to the
 // compensated field pair: a plain FP32 field would add the same drift
 // increment to a value on its own grid every step, a rounding error with a
 // fixed sign. Returns true when the trajectory has finished (passage or cap).
-template <bool WEIGHTED, bool SMEM, bool NIDX = false>
-__device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab)
+template <bool WEIGHTED, bool SMEM, bool NIDX = false, bool DTAB = false>
+__device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab,
+                                        const ModelDev *s_model)
 {
     // noise table: linear interpolation in x (or in time), end values held outside
     float f;
@@ -199,12 +245,7 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
         cb = 0.0f;
         half_cb2 = 0.0f;
     }
-    // drift: V'/V of the piecewise-linear (or exponential) potential
-    const float d = L.x - L.x_star;
-    const bool up = d >= 0.0f;
-    const float a = up ? L.a_plus : L.a_minus;
-    const float b = up ? L.b_plus : L.b_minus;
-    const float vpv = __fdividef(a, fmaf(b, d, 1.0f));
+    const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model);
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
     const float zb = z + cb;                             // xi + alpha sqrt(dN)
     const float dx = fmaf(S, zb, L.p * L.dN);           // (pi + alpha S) dN + S xi sqrt(dN)
@@ -354,8 +395,8 @@ __device__ __forceinline__ bool past_deadline(const EmParams &P, unsigned long l
 // Register budgets: the plain stepper keeps three 512-thread blocks per SM
 // (48 warps); the learned-proposal stepper at most 384 threads per block and
 // two resident blocks, so that the network's registers still leave 24 warps.
-template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX>
-__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 3) em_kernel(const EmParams P)
+template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX, bool DTAB>
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3) em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
@@ -392,7 +433,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX) ? 2 : 
             for (int s = 0; s < 4; ++s)
                 if (active && !done) {
                     if (REC) sg.sum_xi += z[s];
-                    done = em_step<WEIGHTED, SMEM, NIDX>(L, z[s], tab);
+                    done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model);
                 }
         }
 
@@ -454,16 +495,13 @@ __device__ __forceinline__ void table2_at(const Lane &L, const float4 *__restric
     c = fmaf(f, e1.z - e0.z, e0.z);
 }
 
-template <bool WEIGHTED, bool SMEM>
-__device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const float4 *__restrict__ tab)
+template <bool WEIGHTED, bool SMEM, bool DTAB>
+__device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const float4 *__restrict__ tab,
+                                         const ModelDev *s_model)
 {
     float a, b, c;                                       // S sqrt(dN), interpolated in x
     table2_at<SMEM>(L, tab, a, b, c);
-    const float d = L.x - L.x_star;
-    const bool up = d >= 0.0f;
-    const float sa = up ? L.a_plus : L.a_minus;
-    const float sb = up ? L.b_plus : L.b_minus;
-    const float vpv = __fdividef(sa, fmaf(sb, d, 1.0f));
+    const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model);
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
     const float e1 = z1 + L.cb, e2 = z2 + L.cb_b;       // xi + beta sqrt(dN)
     // (phi, pi) += D dN + S beta dN + S xi sqrt(dN) = D dN + (S sqrt(dN)) e
@@ -499,7 +537,7 @@ __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, const uin
     }
 }
 
-template <bool WEIGHTED, bool SMEM, bool MLP>
+template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB>
 __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
@@ -523,16 +561,17 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
             mlp2_segment_start(L, active && L.mlp, s_tiles, s_bias, prun);
 
         for (int g = 0; g < P.groups_per_check; ++g) {
-            // four steps per group (L.n is a multiple of 4 here): Philox blocks n/2, n/2 + 1
+            // four steps per group, two per Philox block: L.n is even at each block
+            // (a lane that finished keeps its count and ignores the normals)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint4 r = philox4x32_10(make_uint4(((uint32_t)L.n >> 1) + (uint32_t)h, L.traj, L.run_id, 0u),
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 1, L.traj, L.run_id, 0u),
                                               P.key_lo, P.key_hi);
                 float z[4];
                 box_muller(r.x, r.y, z[0], z[1]);
                 box_muller(r.z, r.w, z[2], z[3]);
-                if (active && !done) done = em2_step<WEIGHTED, SMEM>(L, z[0], z[1], tab);
-                if (active && !done) done = em2_step<WEIGHTED, SMEM>(L, z[2], z[3], tab);
+                if (active && !done) done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model);
+                if (active && !done) done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model);
             }
         }
         refill_point(P, L, active, done, s_run, s_model);
@@ -541,27 +580,37 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
     }
 }
 
-static const void *em_fn(EmVariant v)
+template <bool DTAB>
+static const void *em_fn_t(EmVariant v)
 {
     if (v.rank2) {
-        if (v.mlp) return v.smem ? (const void *)em2_kernel<true, true, true> : (const void *)em2_kernel<true, false, true>;
-        if (v.weighted) return v.smem ? (const void *)em2_kernel<true, true, false> : (const void *)em2_kernel<true, false, false>;
-        return v.smem ? (const void *)em2_kernel<false, true, false> : (const void *)em2_kernel<false, false, false>;
+        if (v.mlp) return v.smem ? (const void *)em2_kernel<true, true, true, DTAB>
+                                 : (const void *)em2_kernel<true, false, true, DTAB>;
+        if (v.weighted) return v.smem ? (const void *)em2_kernel<true, true, false, DTAB>
+                                      : (const void *)em2_kernel<true, false, false, DTAB>;
+        return v.smem ? (const void *)em2_kernel<false, true, false, DTAB>
+                      : (const void *)em2_kernel<false, false, false, DTAB>;
     }
-    if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true, false>
-                             : (const void *)em_kernel<true, false, true, true, false>;
-    if (v.mlp) return v.smem ? (const void *)em_kernel<true, true, true, false, false>
-                             : (const void *)em_kernel<true, false, true, false, false>;
-    if (v.nidx) {
-        if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, true>
-                                      : (const void *)em_kernel<true, false, false, false, true>;
-        return v.smem ? (const void *)em_kernel<false, true, false, false, true>
-                      : (const void *)em_kernel<false, false, false, false, true>;
+    if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true, false, DTAB>
+                             : (const void *)em_kernel<true, false, true, true, false, DTAB>;
+    if (v.mlp) return v.smem ? (const void *)em_kernel<true, true, true, false, false, DTAB>
+                             : (const void *)em_kernel<true, false, true, false, false, DTAB>;
+    if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, false, DTAB>
+                                  : (const void *)em_kernel<true, false, false, false, false, DTAB>;
+    return v.smem ? (const void *)em_kernel<false, true, false, false, false, DTAB>
+                  : (const void *)em_kernel<false, false, false, false, false, DTAB>;
+}
+
+static const void *em_fn(EmVariant v)
+{
+    if (v.dtab) return em_fn_t<true>(v);
+    if (v.nidx && !v.rank2 && !v.mlp) {
+        if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, true, false>
+                                      : (const void *)em_kernel<true, false, false, false, true, false>;
+        return v.smem ? (const void *)em_kernel<false, true, false, false, true, false>
+                      : (const void *)em_kernel<false, false, false, false, true, false>;
     }
-    if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, false>
-                                  : (const void *)em_kernel<true, false, false, false, false>;
-    return v.smem ? (const void *)em_kernel<false, true, false, false, false>
-                  : (const void *)em_kernel<false, false, false, false, false>;
+    return em_fn_t<false>(v);
 }
 
 // Opt in to the dynamic shared memory the table (and proposal) need, outside

@@ -42,9 +42,33 @@ static const double kBdRatio = 100.0;  // k/(aH) at the Bunch-Davies start, time
 // ---------------------------------------------------------------------------
 // Potential
 // ---------------------------------------------------------------------------
+// Gaussian bump, Eq. (4.12): V = V0 f (1 + g), f = phi^2/(m^2 + phi^2),
+// g = K exp(-(phi - phi0)^2/(2 w^2)); f'/f = 2 m^2/(phi (m^2 + phi^2)),
+// f''/f = 2 m^2 (m^2 - 3 phi^2)/(phi^2 (m^2 + phi^2)^2), g' = -g (phi - phi0)/w^2,
+// g'' = g ((phi - phi0)^2/w^2 - 1)/w^2.
+struct BumpTerms { double f1, f2, g, g1, g2, f; };
+
+static BumpTerms bump_terms(const fpt_model &m, double phi)
+{
+    BumpTerms b;
+    const double m2 = m.bump_m * m.bump_m, w2 = m.bump_width * m.bump_width, d = phi - m.bump_phi0;
+    const double q = m2 + phi * phi;
+    b.f = phi * phi / q;
+    b.g = m.bump_K * std::exp(-0.5 * d * d / w2);
+    b.f1 = 2.0 * m2 / (phi * q);
+    b.f2 = 2.0 * m2 * (m2 - 3.0 * phi * phi) / (phi * phi * q * q);
+    b.g1 = -b.g * d / w2;
+    b.g2 = b.g * (d * d / w2 - 1.0) / w2;
+    return b;
+}
+
 double dlnV(const fpt_model &m, double phi, int branch)
 {
     if (m.kind == FPT_POT_EXP) return m.mu;
+    if (m.kind == FPT_POT_BUMP) {
+        const BumpTerms b = bump_terms(m, phi);
+        return b.f1 + b.g1 / (1.0 + b.g);
+    }
     bool above = branch == 0 ? (phi >= m.phi_star) : (branch > 0);
     double a = above ? m.a_plus : m.a_minus;
     return a / (1.0 + a * (phi - m.phi_star));
@@ -53,14 +77,24 @@ double dlnV(const fpt_model &m, double phi, int branch)
 double Vof(const fpt_model &m, double phi, int branch)
 {
     if (m.kind == FPT_POT_EXP) return m.V0 * std::exp(m.mu * phi);
+    if (m.kind == FPT_POT_BUMP) {
+        const BumpTerms b = bump_terms(m, phi);
+        return m.V0 * b.f * (1.0 + b.g);
+    }
     bool above = branch == 0 ? (phi >= m.phi_star) : (branch > 0);
     double a = above ? m.a_plus : m.a_minus;
     return m.V0 * (1.0 + a * (phi - m.phi_star));
 }
 
-static double d2lnV_term(const fpt_model &m)  // V''/V away from the kink
+// V''/V (away from the kink of the piecewise-linear potential, where it vanishes)
+double d2V_over_V(const fpt_model &m, double phi)
 {
-    return m.kind == FPT_POT_EXP ? m.mu * m.mu : 0.0;
+    if (m.kind == FPT_POT_EXP) return m.mu * m.mu;
+    if (m.kind == FPT_POT_BUMP) {
+        const BumpTerms b = bump_terms(m, phi);
+        return b.f2 + (2.0 * b.f1 * b.g1 + b.g2) / (1.0 + b.g);
+    }
+    return 0.0;
 }
 
 double hubble(const fpt_model &m, double phi, double pi, int branch)
@@ -122,9 +156,11 @@ struct DP5 {
 
     // Adaptive integration from t0 to t1 (t1 > t0). on_step(t, y, f) is
     // called for the initial point and every accepted step.
+    // stop(t, y, f), when given, ends the integration after an accepted step.
     static void integrate(const Rhs &f, double t0, double t1, Vec &y, double rtol, const Vec &atol,
                           double h0, double hmax,
-                          const std::function<void(double, const Vec &, const Vec &)> &on_step = nullptr)
+                          const std::function<void(double, const Vec &, const Vec &)> &on_step = nullptr,
+                          const std::function<bool(double, const Vec &, const Vec &)> &stop = nullptr)
     {
         Vec f0, y1, f1;
         double t = t0, h = std::min(h0, t1 - t0);
@@ -146,6 +182,7 @@ struct DP5 {
             y = y1;
             f0 = f1;
             if (on_step) on_step(t, y, f0);
+            if (stop && stop(t, y, f0)) return;
             double fac = err > 0 ? std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2))) : 5.0;
             h = std::min(h * fac, hmax);
         }
@@ -218,6 +255,36 @@ static Background solve_background(const fpt_model &m, double phi0, double N_spa
             v.push_back({N, yy[0], yy[1], ff[0], ff[1]});
         };
     };
+    if (m.kind == FPT_POT_BUMP) {
+        // smooth potential: N_T marks the onset of ultra-slow roll, the first
+        // time eps2 = 2 pi'/pi reaches -3 (Sec. 4.3)
+        D2::Rhs f = [&](double t, const std::array<double, 2> &yy, std::array<double, 2> &ff) {
+            bg_rhs(m, 0, t, yy, ff);
+        };
+        // stop at the onset, or when inflation ends (eps1 = 1) without one
+        auto usr = [](double, const std::array<double, 2> &yy, const std::array<double, 2> &ff) {
+            return 2.0 * ff[1] / yy[1] <= -3.0 || 0.5 * yy[1] * yy[1] >= 1.0;
+        };
+        D2::integrate(f, 0.0, 400.0, y, kBgRtol, atol, 1e-4, kBgHmax, push(bg.post), usr);
+        const size_t n = bg.post.size();
+        if (n < 2 || !(2.0 * bg.post[n - 1].dpi / bg.post[n - 1].pi <= -3.0))
+            throw std::runtime_error("the background never enters ultra-slow roll (eps2 > -3 throughout)");
+        const BgPoint a = bg.post[n - 2], b = bg.post[n - 1];
+        double lo = a.N, hi = b.N;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi), ph, pi;
+            Background::hermite(a, b, mid, ph, pi);
+            std::array<double, 2> ff;
+            bg_rhs(m, 0, mid, {ph, pi}, ff);
+            if (2.0 * ff[1] / pi > -3.0) lo = mid; else hi = mid;
+        }
+        bg.N_T = 0.5 * (lo + hi);
+        bg.kink = false;
+        // continue from the last accepted point (its duplicate is dropped)
+        bg.post.pop_back();
+        D2::integrate(f, b.N, bg.N_T + N_span, y, kBgRtol, atol, 1e-4, kBgHmax, push(bg.post));
+        return bg;
+    }
     if (!has_kink) {
         D2::Rhs f = [&](double t, const std::array<double, 2> &yy, std::array<double, 2> &ff) {
             bg_rhs(m, 0, t, yy, ff);
@@ -279,9 +346,10 @@ static Resolved resolve_full(const fpt_model &m)
 {
     Resolved r;
     if (!std::isnan(m.n_in)) {
-        r.bg = solve_background(m, m.bg_phi0, std::max(60.0, 2.0 * m.n_end + 40.0));
+        const double span = m.kind == FPT_POT_BUMP ? m.n_end + 10.0 : std::max(60.0, 2.0 * m.n_end + 40.0);
+        r.bg = solve_background(m, m.bg_phi0, span);
         r.has_bg = true;
-        if (!r.bg.kink) throw std::runtime_error("transition rule needs bg_phi0 > phi_star");
+        if (!r.bg.kink && m.kind != FPT_POT_BUMP) throw std::runtime_error("transition rule needs bg_phi0 > phi_star");
         r.N_in = r.bg.N_T + m.n_in;
         r.N_end = r.bg.N_T + m.n_end;
         int br;
@@ -325,7 +393,7 @@ static void mode_rhs(const fpt_model &m, double k, int branch, double N,
     double H2 = V / (3.0 - 0.5 * pi * pi);
     double eps1 = 0.5 * pi * pi;
     double dpi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi, branch));
-    double mass = (k * k) / (std::exp(2.0 * N) * H2) + d2lnV_term(m) * V / H2
+    double mass = (k * k) / (std::exp(2.0 * N) * H2) + d2V_over_V(m, phi) * V / H2
                   - (3.0 - eps1) * pi * pi - 2.0 * pi * dpi;
     f[0] = pi;
     f[1] = dpi;
@@ -376,7 +444,7 @@ static double nu_squared(const fpt_model &m, double phi, double pi, int branch)
     double dpi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi, branch));
     double eps2 = 2.0 * dpi / pi;
     double v1 = dlnV(m, phi, branch);
-    return 2.25 - eps1 - 0.5 * eps1 * eps2 * eps2 / (3.0 - eps1) + (eps1 - 3.0) * (d2lnV_term(m) - v1 * v1);
+    return 2.25 - eps1 - 0.5 * eps1 * eps2 * eps2 / (3.0 - eps1) + (eps1 - 3.0) * (d2V_over_V(m, phi) - v1 * v1);
 }
 
 // Run fn(j) for j = 0 .. n-1 on a pool of host threads; the first exception
@@ -483,24 +551,33 @@ static void numeric_noise(const fpt_model &m, const Resolved &r, double phi, dou
 // ---------------------------------------------------------------------------
 std::string validate_model(const fpt_model &m)
 {
-    if (m.kind != FPT_POT_PWLINEAR && m.kind != FPT_POT_EXP) return "unknown potential kind";
+    if (m.kind != FPT_POT_PWLINEAR && m.kind != FPT_POT_EXP && m.kind != FPT_POT_BUMP) return "unknown potential kind";
     if (!(m.V0 > 0) || !std::isfinite(m.V0)) return "V0 must be positive and finite";
     if (!(m.dN > 0) || !std::isfinite(m.dN)) return "dN must be positive";
     if (m.max_steps < 1 || m.max_steps >= (int64_t(1) << 31)) return "max_steps out of [1, 2^31)";
     if (m.kind == FPT_POT_PWLINEAR) {
         if (!std::isfinite(m.a_plus) || !std::isfinite(m.a_minus) || !std::isfinite(m.phi_star))
             return "slopes and phi_star must be finite";
-    } else if (!std::isfinite(m.mu)) {
-        return "mu must be finite";
+    } else if (m.kind == FPT_POT_EXP) {
+        if (!std::isfinite(m.mu)) return "mu must be finite";
+    } else {
+        if (!std::isfinite(m.bump_K) || !(m.bump_K > -1.0) || !(m.bump_m > 0) || !std::isfinite(m.bump_m) ||
+            !(m.bump_width > 0) || !std::isfinite(m.bump_width) || !std::isfinite(m.bump_phi0))
+            return "bump parameters: need K > -1, m > 0, width > 0, finite phi0";
     }
     if (!std::isnan(m.n_in)) {
-        if (m.kind != FPT_POT_PWLINEAR) return "the transition rule needs a piecewise-linear potential";
+        if (m.kind == FPT_POT_EXP) return "the transition rule needs a piecewise-linear or bump potential";
         if (!(m.n_end > m.n_in) || !(m.n_in >= 0) || !(m.n_end < 200)) return "need 0 <= n_in < n_end < 200";
-        if (!(m.bg_phi0 > m.phi_star)) return "the transition rule needs bg_phi0 > phi_star";
-        if (!(m.a_plus > 0) || !(m.a_minus > 0)) return "the transition rule needs positive slopes";
+        if (m.kind == FPT_POT_PWLINEAR) {
+            if (!(m.bg_phi0 > m.phi_star)) return "the transition rule needs bg_phi0 > phi_star";
+            if (!(m.a_plus > 0) || !(m.a_minus > 0)) return "the transition rule needs positive slopes";
+        } else if (!(m.bg_phi0 > 0) || !std::isfinite(m.bg_phi0)) {
+            return "the transition rule needs a positive bg_phi0";
+        }
     } else {
         if (!std::isfinite(m.phi_in) || !std::isfinite(m.phi_end)) return "phi_in and phi_end must be finite";
         if (!(m.phi_in > m.phi_end)) return "need phi_in > phi_end";
+        if (m.kind == FPT_POT_BUMP && !(m.phi_end > 0)) return "the bump potential needs phi_end > 0";
         if (!std::isnan(m.pi_in) && !std::isfinite(m.pi_in)) return "pi_in must be finite or NaN";
     }
     return "";

@@ -23,7 +23,7 @@ NAN = float("nan")
 
 FPT_OK, FPT_E_INVALID, FPT_E_CUDA, FPT_E_NOMEM, FPT_E_TIMEOUT, FPT_E_STATE = 0, 1, 2, 3, 4, 5
 FPT_W_CAPPED = 100
-FPT_POT_PWLINEAR, FPT_POT_EXP = 0, 1
+FPT_POT_PWLINEAR, FPT_POT_EXP, FPT_POT_BUMP = 0, 1, 2
 FPT_TABLE_DESITTER, FPT_TABLE_BESSEL, FPT_TABLE_USER, FPT_TABLE_BESSEL_N, FPT_TABLE_USER_N = 0, 1, 2, 3, 4
 FPT_TABLE_NUMERIC, FPT_TABLE_USER2 = 5, 6
 FPT_BIAS_NONE, FPT_BIAS_CONST, FPT_BIAS_MLP = 0, 1, 2
@@ -45,7 +45,9 @@ class fpt_model(C.Structure):
                 ("a_plus", C.c_double), ("a_minus", C.c_double), ("phi_star", C.c_double),
                 ("mu", C.c_double), ("phi_in", C.c_double), ("pi_in", C.c_double),
                 ("phi_end", C.c_double), ("bg_phi0", C.c_double), ("n_in", C.c_double),
-                ("n_end", C.c_double), ("dN", C.c_double), ("max_steps", C.c_int64)]
+                ("n_end", C.c_double), ("dN", C.c_double), ("max_steps", C.c_int64),
+                ("bump_K", C.c_double), ("bump_m", C.c_double), ("bump_width", C.c_double),
+                ("bump_phi0", C.c_double)]
 
 
 class fpt_model_info(C.Structure):
@@ -206,7 +208,9 @@ def model_struct(m) -> fpt_model:
                      a_minus=get("a_minus", 0.0), phi_star=get("phi_star", 0.0), mu=get("mu", 0.0),
                      phi_in=get("phi_in"), pi_in=get("pi_in"), phi_end=get("phi_end"),
                      bg_phi0=get("bg_phi0"), n_in=get("n_in"), n_end=get("n_end"), dN=get("dN"),
-                     max_steps=int(get("max_steps", 1 << 20)))
+                     max_steps=int(get("max_steps", 1 << 20)), bump_K=get("bump_K", 0.0),
+                     bump_m=get("bump_m", 0.0), bump_width=get("bump_width", 0.0),
+                     bump_phi0=get("bump_phi0", 0.0))
 
 
 class Context:

@@ -171,3 +171,32 @@ def test_numeric_table_arguments():
         fpt.fpt_table_build2(W.USR_MODEL, fpt.FPT_TABLE_USER2, 16, 1.0)       # user tables are not built
     with pytest.raises(fpt.FptError):
         fpt.fpt_table_build2(W.USR_MODEL, fpt.FPT_TABLE_NUMERIC, 16, 0.0)
+
+
+def test_bump_model_resolution_and_tables_match_oracle():
+    """Gaussian bump (Sec. 4.3): start/end from the ultra-slow-roll onset and the
+    Bessel-matched and numerically matched tables, host builder vs oracle."""
+    m = W.BUMP_MODEL
+    info = fpt.fpt_resolve_model(m)
+    r = T.resolve(m)
+    assert abs(info["N_T"] - r.N_T) < 1e-8
+    assert abs(info["phi_in"] - r.phi_in) < 1e-12 and abs(info["phi_end"] - r.phi_end) < 1e-12
+    assert abs(info["pi_in"] / r.pi_in - 1) < 1e-8
+    idx = [0, 511, 1023]
+    S, Sp = fpt.fpt_table_build(m, fpt.FPT_TABLE_BESSEL, 1024, 1.0)
+    tab = T.bessel_table(m, r, 1024, 1.0, indices=idx)
+    np.testing.assert_allclose(S[idx], tab.S[idx], rtol=1e-8)
+    np.testing.assert_allclose(Sp[idx], tab.T[idx], rtol=1e-8)
+    Spp, Spq, Sqq = fpt.fpt_table_build2(m, fpt.FPT_TABLE_NUMERIC, 1024, 1.0)
+    t2 = T.numeric_table(m, r, 1024, 1.0, indices=idx)
+    for got, ref in ((Spp, t2.Spp), (Spq, t2.Spq), (Sqq, t2.Sqq)):
+        np.testing.assert_allclose(got[idx], ref[idx], rtol=1e-7)
+
+
+def test_bump_model_arguments():
+    import dataclasses
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_resolve_model(dataclasses.replace(W.BUMP_MODEL, bump_width=0.0))
+    with pytest.raises(fpt.FptError) as e:
+        fpt.fpt_resolve_model(dataclasses.replace(W.BUMP_MODEL, bg_phi0=2.19))   # starts past the bump: no USR onset
+    assert "ultra-slow roll" in str(e.value)
