@@ -97,7 +97,8 @@ struct RunSm {               // per-run constants staged in shared memory
 
 struct Lane {                // per-thread trajectory state and its constants
     float x, x_c;            // shifted field phi - phi_end as a Kahan pair: x - x_c
-    float p, lw_hi, lw_lo;
+    float p, p_c;            // momentum; p_c compensates it (Kahan) in the variants with pi-noise
+    float lw_hi, lw_lo;
     int n;
     int nmax;
     uint32_t traj, run_id;
@@ -164,6 +165,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.x = m.x_in;
     L.x_c = 0.0f;
     L.p = m.pi_in;
+    L.p_c = 0.0f;
     L.lw_hi = 0.0f;
     L.lw_lo = 0.0f;
     L.n = 0;
@@ -249,10 +251,15 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
     const float zb = z + cb;                             // xi + alpha sqrt(dN)
     const float dx = fmaf(S, zb, L.p * L.dN);           // (pi + alpha S) dN + S xi sqrt(dN)
-    const float pn = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
+    if (DTAB) {
+        // correlated pi-noise (tan theta_n ~ 0.3): the momentum is a compensated
+        // pair, or its rounding performs a random walk that the field integrates
+        kahan_add(L.p, L.p_c, fmaf(T, zb, hh * L.dN * (L.p + vpv)));
+    } else {
+        L.p = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
+    }
     if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(cb, z, half_cb2));
     kahan_add(L.x, L.x_c, dx);
-    L.p = pn;
     ++L.n;
     return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= L.nmax);
 }
@@ -506,10 +513,10 @@ __device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const floa
     const float e1 = z1 + L.cb, e2 = z2 + L.cb_b;       // xi + beta sqrt(dN)
     // (phi, pi) += D dN + S beta dN + S xi sqrt(dN) = D dN + (S sqrt(dN)) e
     const float dx = fmaf(a, e1, fmaf(b, e2, L.p * L.dN));
-    const float pn = fmaf(b, e1, fmaf(c, e2, fmaf(hh * L.dN, L.p + vpv, L.p)));
+    // full-rank noise drives pi directly: compensated momentum (see em_step)
+    kahan_add(L.p, L.p_c, fmaf(b, e1, fmaf(c, e2, hh * L.dN * (L.p + vpv))));
     if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2)));
     kahan_add(L.x, L.x_c, dx);
-    L.p = pn;
     ++L.n;
     return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= L.nmax);
 }

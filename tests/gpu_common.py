@@ -48,7 +48,11 @@ def compare(g, o, x_in, label="", max_mismatch=MAX_MISMATCH, max_step_diff=None)
     near = (o.xmin_pre <= tau) | (x_final > -tau)
     mism = g["nsteps"].astype(np.int64) != o.nsteps
     bad = mism & ~near
-    assert not bad.any(), f"{label}: {bad.sum()} non-near-tie step mismatches, e.g. {np.flatnonzero(bad)[:5]}"
+    if bad.any():
+        j = np.flatnonzero(bad)[:5]
+        detail = ", ".join(f"#{i}: gpu {g['nsteps'][i]} oracle {o.nsteps[i]} xmin_pre/tau "
+                           f"{o.xmin_pre[i] / tau:.3g} x_final/tau {x_final[i] / tau:.3g}" for i in j)
+        raise AssertionError(f"{label}: {bad.sum()} non-near-tie step mismatches: {detail}")
     assert mism.mean() <= max_mismatch, f"{label}: mismatch fraction {mism.mean():.4f}"
     if max_step_diff is not None and mism.any():
         d = np.abs(g["nsteps"].astype(np.int64) - o.nsteps)[mism]

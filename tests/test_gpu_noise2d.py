@@ -92,7 +92,7 @@ def test_2d_numeric_table_matches_oracle_and_runs(torch):
         np.testing.assert_allclose(Spq, tab.Spq, rtol=1e-7, atol=1e-7 * np.max(np.abs(tab.Spq)))
         np.testing.assert_allclose(Sqq, tab.Sqq, rtol=1e-7)
         st, g = gpu_run(ctx, [fpt.run_desc(0, n, seed=82, A=0.7, A2=0.2)], [n])
-        assert st == fpt.FPT_OK
+        assert st in (fpt.FPT_OK, fpt.FPT_W_CAPPED)
     o = OS.run2(m, res, tab, seed=82, run_id=0, n=n, A=0.7, A2=0.2)
     o.phi_end_value = res.phi_end
     compare(g[0], o, res.phi_in - res.phi_end, "2-D numeric table")
