@@ -213,6 +213,46 @@ fpt_status fpt_table_build2(const fpt_model *model, int32_t kind, int32_t n_poin
                             double sigma, double phi_lo, double phi_hi, double *out_S);
 
 /*
+ * ---- Classical delta N (Sec. 2.2), host only, FP64 ----
+ * The comparison the paper draws between the stochastic P(delta N) and the
+ * classical delta-N formalism: the linear power spectrum of Eq. (2.8),
+ * P_R = k^3/(2 pi^2) |delta phi_k|^2 / (2 eps1), from the mode of Eq. (2.4)
+ * (Bunch-Davies start, Eq. 2.5, at k/(aH) = 100/sigma, kink jump as for the
+ * tables); its variance over the simulated mode range, Eq. (2.18); and the
+ * constant-eps2 PDF of Eq. (2.20). Models need the transition rule.
+ */
+
+/* P_R of the modes k = sigma a H at background times N_s[j] (n entries, host),
+ * read at N_eval (NaN: N_end + 4, outside the Hubble radius). */
+fpt_status fpt_power_spectrum(const fpt_model *model, double sigma, int32_t n, const double *N_s,
+                              double N_eval, double *out_PR);
+
+typedef struct {
+    double sigma_R2;       /* int P_R d ln k over the modes reaching sigma a H in
+                              [N_in, N_end] (composite Simpson, n_k points)   */
+    double eps2_in;        /* eps2 = 2 pi'/pi of the background at N_in       */
+    double eps2_end;       /* ... and at N_end                               */
+    double N_in, N_end;    /* background times of phi_in and phi_end          */
+} fpt_classical;
+
+/* n_k odd in [3, 4097]; N_eval as fpt_power_spectrum. */
+fpt_status fpt_classical_dn(const fpt_model *model, double sigma, int32_t n_k, double N_eval,
+                            fpt_classical *out);
+
+/* Eq. (2.20) at dN[i] (host, n entries): P(dN) = exp[-(2/(sigma_R2 eps2^2))
+ * (1 - e^{-eps2 dN/2})^2 - eps2 dN/2] / sqrt(2 pi sigma_R2); eps2 = 0 gives
+ * the Gaussian of variance sigma_R2. */
+fpt_status fpt_classical_pdf(const double *dN, int64_t n, double sigma_R2, double eps2, double *out);
+
+/* Least-squares eps2 of Eq. (2.20) to a measured P(dN): minimises
+ * sum_b ((ln pdf_b - ln P(dN_b))/(se_b/pdf_b))^2 over bins with pdf, se > 0
+ * by golden-section search on [eps2_lo, eps2_hi] (the paper's fitted curves,
+ * Sec. 4.3). chi2_out, bins_used nullable. All arrays host, n_bins entries. */
+fpt_status fpt_fit_eps2(const double *dN, const double *pdf, const double *se, int32_t n_bins,
+                        double sigma_R2, double eps2_lo, double eps2_hi, double *eps2_out,
+                        double *chi2_out, int32_t *bins_used);
+
+/*
  * One run: a set of trajectories of one model with one bias.
  *
  * The noise of step i of trajectory t is drawn from Philox4x32-10 with key

@@ -378,6 +378,106 @@ fpt_status fpt_table_build2(const fpt_model *model, int32_t kind, int32_t n_poin
     return FPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Classical delta N (host only)
+// ---------------------------------------------------------------------------
+fpt_status fpt_power_spectrum(const fpt_model *model, double sigma, int32_t n, const double *N_s,
+                              double N_eval, double *out_PR)
+{
+    if (!model || !N_s || !out_PR || n < 0) return fail(nullptr, FPT_E_INVALID, "null argument or negative n");
+    if (!(sigma > 0 && sigma <= 10)) return fail(nullptr, FPT_E_INVALID, "sigma out of (0, 10]");
+    fpt_model_info info;
+    fpt_status s = fpt_resolve_model(model, &info);
+    if (s != FPT_OK) return s;
+    try {
+        fpt_host::power_spectrum(*model, sigma, n, N_s, N_eval, out_PR);
+    } catch (const std::exception &e) {
+        return fail(nullptr, FPT_E_INVALID, e.what());
+    }
+    return FPT_OK;
+}
+
+fpt_status fpt_classical_dn(const fpt_model *model, double sigma, int32_t n_k, double N_eval,
+                            fpt_classical *out)
+{
+    if (!model || !out) return fail(nullptr, FPT_E_INVALID, "null argument");
+    if (n_k < 3 || n_k > 4097 || !(n_k & 1)) return fail(nullptr, FPT_E_INVALID, "n_k must be odd in [3, 4097]");
+    if (!(sigma > 0 && sigma <= 10)) return fail(nullptr, FPT_E_INVALID, "sigma out of (0, 10]");
+    fpt_model_info info;
+    fpt_status s = fpt_resolve_model(model, &info);
+    if (s != FPT_OK) return s;
+    try {
+        fpt_host::classical_dn(*model, sigma, n_k, N_eval, out->sigma_R2, out->eps2_in, out->eps2_end,
+                               out->N_in, out->N_end);
+    } catch (const std::exception &e) {
+        return fail(nullptr, FPT_E_INVALID, e.what());
+    }
+    return FPT_OK;
+}
+
+// Eq. (2.20); eps2 = 0 is the Gaussian limit.
+static double classical_pdf_one(double dN, double s2, double eps2)
+{
+    const double c = 1.0 / std::sqrt(2.0 * 3.14159265358979323846 * s2);
+    if (eps2 == 0.0) return c * std::exp(-dN * dN / (2.0 * s2));
+    const double R = -(2.0 / eps2) * -std::expm1(-0.5 * eps2 * dN);
+    return c * std::exp(-R * R / (2.0 * s2) - 0.5 * eps2 * dN);
+}
+
+fpt_status fpt_classical_pdf(const double *dN, int64_t n, double sigma_R2, double eps2, double *out)
+{
+    if ((!dN || !out) && n > 0) return fail(nullptr, FPT_E_INVALID, "null argument");
+    if (n < 0 || !(sigma_R2 > 0) || !std::isfinite(sigma_R2) || !std::isfinite(eps2))
+        return fail(nullptr, FPT_E_INVALID, "need n >= 0, sigma_R2 > 0 and finite eps2");
+    for (int64_t i = 0; i < n; ++i) out[i] = classical_pdf_one(dN[i], sigma_R2, eps2);
+    return FPT_OK;
+}
+
+// chi^2 of ln P: sum over bins with pdf > 0 and se > 0 of
+// ((ln pdf_b - ln P(dN_b; sigma_R2, eps2)) / (se_b / pdf_b))^2.
+static double fit_chi2(const double *dN, const double *pdf, const double *se, int n, double s2, double e2,
+                       int *used)
+{
+    double chi2 = 0.0;
+    int k = 0;
+    for (int b = 0; b < n; ++b) {
+        if (!(pdf[b] > 0) || !(se[b] > 0)) continue;
+        const double lp = std::log(classical_pdf_one(dN[b], s2, e2));
+        const double r = (std::log(pdf[b]) - lp) * pdf[b] / se[b];
+        chi2 += r * r;
+        ++k;
+    }
+    if (used) *used = k;
+    return chi2;
+}
+
+fpt_status fpt_fit_eps2(const double *dN, const double *pdf, const double *se, int32_t n_bins,
+                        double sigma_R2, double eps2_lo, double eps2_hi, double *eps2_out,
+                        double *chi2_out, int32_t *bins_used)
+{
+    if (!dN || !pdf || !se || !eps2_out || n_bins < 1) return fail(nullptr, FPT_E_INVALID, "null argument or no bins");
+    if (!(sigma_R2 > 0) || !(eps2_hi > eps2_lo) || !std::isfinite(eps2_lo) || !std::isfinite(eps2_hi))
+        return fail(nullptr, FPT_E_INVALID, "need sigma_R2 > 0 and eps2_lo < eps2_hi");
+    // golden-section search for the minimum of chi^2 on [eps2_lo, eps2_hi]
+    const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+    double a = eps2_lo, b = eps2_hi;
+    double c = b - g * (b - a), d = a + g * (b - a);
+    double fc = fit_chi2(dN, pdf, se, n_bins, sigma_R2, c, nullptr);
+    double fd = fit_chi2(dN, pdf, se, n_bins, sigma_R2, d, nullptr);
+    for (int it = 0; it < 200 && b - a > 1e-12 * std::max(1.0, std::fabs(a)); ++it) {
+        if (fc < fd) { b = d; d = c; fd = fc; c = b - g * (b - a); fc = fit_chi2(dN, pdf, se, n_bins, sigma_R2, c, nullptr); }
+        else { a = c; c = d; fc = fd; d = a + g * (b - a); fd = fit_chi2(dN, pdf, se, n_bins, sigma_R2, d, nullptr); }
+    }
+    const double e = 0.5 * (a + b);
+    int used = 0;
+    const double chi2 = fit_chi2(dN, pdf, se, n_bins, sigma_R2, e, &used);
+    if (used == 0) return fail(nullptr, FPT_E_INVALID, "no bin with pdf > 0 and se > 0");
+    *eps2_out = e;
+    if (chi2_out) *chi2_out = chi2;
+    if (bins_used) *bins_used = used;
+    return FPT_OK;
+}
+
 fpt_status fpt_init_model(fpt_ctx **pctx, const fpt_model *models, int32_t n_models, int32_t device)
 {
     if (!pctx) return fail(nullptr, FPT_E_INVALID, "null ctx pointer");
@@ -495,10 +595,12 @@ static fpt_status upload_tables(fpt_ctx *ctx)
         ModelDev &d = md[i];
         std::memset(&d, 0, sizeof(d));
         d.x_star = (float)(m.phi_star - inf.phi_end);
+        d.x_star_lo = (float)((m.phi_star - inf.phi_end) - (double)d.x_star);
         if (m.kind == FPT_POT_EXP) {
             d.a_plus = d.a_minus = (float)m.mu;
             d.b_plus = d.b_minus = 0.0f;
             d.x_star = 0.0f;
+            d.x_star_lo = 0.0f;
         } else {
             d.a_plus = (float)m.a_plus;
             d.a_minus = (float)m.a_minus;

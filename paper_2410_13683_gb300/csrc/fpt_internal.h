@@ -21,6 +21,9 @@ void build_table(const fpt_model &m, int kind, int n_points, double sigma, doubl
 void build_table2(const fpt_model &m, int kind, int n_points, double sigma, double phi_lo,
                   double phi_hi, std::vector<double> &Spp, std::vector<double> &Spq,
                   std::vector<double> &Sqq, double &lo_out, double &h_out);
+void power_spectrum(const fpt_model &m, double sigma, int n, const double *Ns, double N_eval, double *out);
+void classical_dn(const fpt_model &m, double sigma, int n_k, double N_eval, double &s2,
+                  double &eps2_in, double &eps2_end, double &N_in, double &N_end);
 double dlnV(const fpt_model &m, double phi, int branch);
 double d2V_over_V(const fpt_model &m, double phi);
 double Vof(const fpt_model &m, double phi, int branch);
@@ -40,7 +43,8 @@ constexpr int kMlpMaxBlock = 384;       // block-size cap of the learned-proposa
 
 // Model constants in the shifted coordinate x = phi - phi_end (FP32).
 struct ModelDev {
-    float x_star;              // phi_star - phi_end
+    float x_star;              // phi_star - phi_end (FP32 head)
+    float x_star_lo;           // phi_star - phi_end - x_star (FP32 tail)
     float a_plus, a_minus;     // V'/V = a / (1 + b (x - x_star)), branch by sign
     float b_plus, b_minus;
     float x_in, pi_in;

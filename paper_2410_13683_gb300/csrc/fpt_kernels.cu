@@ -105,7 +105,7 @@ struct Lane {                // per-thread trajectory state and its constants
     float cb, half_cb2, dN, sqrt_dN;
     float cb_b;              // 2-D noise: beta_2 sqrt(dN) (cb = beta_1 sqrt(dN))
     union {                  // drift constants of the lane's potential
-        struct { float x_star, a_plus, a_minus, b_plus, b_minus; } pw;   // piecewise-linear / exponential
+        struct { float x_star, x_star_lo, a_plus, a_minus, b_plus, b_minus; } pw;   // piecewise-linear / exponential
         struct { float scale, umax; int dtab, model; } bump;              // Gaussian bump: cubic V'/V table
     } dc;
     float u_scale, u_shift, u_max;
@@ -149,6 +149,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
         L.dc.bump.model = r.model;
     } else {
         L.dc.pw.x_star = m.x_star;
+        L.dc.pw.x_star_lo = m.x_star_lo;
         L.dc.pw.a_plus = m.a_plus;
         L.dc.pw.a_minus = m.a_minus;
         L.dc.pw.b_plus = m.b_plus;
@@ -202,8 +203,11 @@ __device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restri
                                            const ModelDev *s_model)
 {
     if (!DTAB) {
+        // side of the kink from the compensated field and kink position:
+        // x - x_c >= x_star + x_star_lo (x - x_star is exact near the kink), so
+        // the branch follows the field itself, not the rounding of its FP32 head
         const float d = L.x - L.dc.pw.x_star;
-        const bool up = d >= 0.0f;
+        const bool up = d >= L.x_c + L.dc.pw.x_star_lo;
         const float a = up ? L.dc.pw.a_plus : L.dc.pw.a_minus;
         const float b = up ? L.dc.pw.b_plus : L.dc.pw.b_minus;
         return __fdividef(a, fmaf(b, d, 1.0f));

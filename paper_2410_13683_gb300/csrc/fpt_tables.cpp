@@ -641,4 +641,71 @@ void build_table2(const fpt_model &m, int kind, int n_points, double sigma, doub
     parallel_points(n_points, [&](int j) { numeric_noise(m, r, lo + h * j, sigma, Spp[j], Spq[j], Sqq[j]); });
 }
 
+// ---------------------------------------------------------------------------
+// Classical delta N (Sec. 2.2): linear power spectrum over the simulated mode
+// range, its variance, and the constant-eps2 PDF
+// ---------------------------------------------------------------------------
+// P_R = k^3/(2 pi^2) |delta phi_k|^2 / (2 eps1), Eq. (2.8), of the mode with
+// k = sigma a H at background time Ns, read at N_eval.
+static double power_spectrum_at(const fpt_model &m, const Resolved &r, double Ns, double sigma,
+                                double N_eval)
+{
+    const Background &bg = r.bg;
+    double ph, pi;
+    int br;
+    bg.state(Ns, ph, pi, br);
+    const double k = sigma * std::exp(Ns) * hubble(m, ph, pi, br);
+    const double N0 = Ns - std::log(kBdRatio / sigma);
+    if (N0 < 0.0) throw std::runtime_error("Bunch-Davies start precedes the background start");
+    std::complex<double> u, du;
+    evolve_mode(m, bg, k, N0, N_eval, u, du);
+    double phe, pie;
+    bg.state(N_eval, phe, pie, br);
+    return k * k * k / (2.0 * kPi * kPi) * std::norm(u) / (std::exp(2.0 * N0) * 2.0 * k) / (pie * pie);
+}
+
+void power_spectrum(const fpt_model &m, double sigma, int n, const double *Ns, double N_eval, double *out)
+{
+    Resolved r = resolve_full(m);
+    if (!r.has_bg) throw std::runtime_error("the power spectrum needs the transition rule (n_in set)");
+    if (std::isnan(N_eval)) N_eval = r.N_end + 4.0;
+    if (!(N_eval <= r.bg.N_max())) throw std::runtime_error("N_eval beyond the background");
+    parallel_points(n, [&](int j) { out[j] = power_spectrum_at(m, r, Ns[j], sigma, N_eval); });
+}
+
+// sigma_R^2 = int P_R d ln k, Eq. (2.18), over the modes that reach sigma a H
+// in [N_in, N_end]: d ln k = (1 - eps1) dN_s; composite Simpson rule on n_k
+// (odd) points. Also eps2 = 2 pi'/pi of the background at N_in and N_end.
+void classical_dn(const fpt_model &m, double sigma, int n_k, double N_eval, double &s2,
+                  double &eps2_in, double &eps2_end, double &N_in, double &N_end)
+{
+    Resolved r = resolve_full(m);
+    if (!r.has_bg) throw std::runtime_error("classical delta N needs the transition rule (n_in set)");
+    if (std::isnan(N_eval)) N_eval = r.N_end + 4.0;
+    if (!(N_eval <= r.bg.N_max())) throw std::runtime_error("N_eval beyond the background");
+    std::vector<double> f(n_k);
+    const double h = (r.N_end - r.N_in) / (n_k - 1);
+    parallel_points(n_k, [&](int j) {
+        const double N = r.N_in + h * j;
+        double ph, pi;
+        int br;
+        r.bg.state(N, ph, pi, br);
+        f[j] = power_spectrum_at(m, r, N, sigma, N_eval) * (1.0 - 0.5 * pi * pi);
+    });
+    double acc = f[0] + f[n_k - 1];
+    for (int j = 1; j < n_k - 1; ++j) acc += (j & 1 ? 4.0 : 2.0) * f[j];
+    s2 = acc * h / 3.0;
+    auto eps2 = [&](double N) {
+        double ph, pi;
+        int br;
+        r.bg.state(N, ph, pi, br);
+        const double dpi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, ph, br));
+        return 2.0 * dpi / pi;
+    };
+    eps2_in = eps2(r.N_in);
+    eps2_end = eps2(r.N_end);
+    N_in = r.N_in;
+    N_end = r.N_end;
+}
+
 }  // namespace fpt_host

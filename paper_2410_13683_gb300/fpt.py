@@ -63,6 +63,11 @@ class fpt_run_desc(C.Structure):
                 ("alpha_max", C.c_float), ("mlp_flags", C.c_int32), ("A2", C.c_double)]
 
 
+class fpt_classical(C.Structure):
+    _fields_ = [("sigma_R2", C.c_double), ("eps2_in", C.c_double), ("eps2_end", C.c_double),
+                ("N_in", C.c_double), ("N_end", C.c_double)]
+
+
 class fpt_traj_out(C.Structure):
     _fields_ = [("N", C.c_void_p), ("logw", C.c_void_p), ("nsteps", C.c_void_p),
                 ("status", C.c_void_p)]
@@ -112,6 +117,14 @@ _SIGNATURES = {
                                    C.c_double, C.c_double, C.c_void_p]),
     "fpt_table_build": (C.c_int, [C.POINTER(fpt_model), C.c_int32, C.c_int32, C.c_double,
                                   C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "fpt_power_spectrum": (C.c_int, [C.POINTER(fpt_model), C.c_double, C.c_int32, C.c_void_p,
+                                     C.c_double, C.c_void_p]),
+    "fpt_classical_dn": (C.c_int, [C.POINTER(fpt_model), C.c_double, C.c_int32, C.c_double,
+                                   C.POINTER(fpt_classical)]),
+    "fpt_classical_pdf": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_void_p]),
+    "fpt_fit_eps2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
+                               C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_int32)]),
     "fpt_set_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
     "fpt_get_launch": (C.c_int, [C.c_void_p, C.POINTER(fpt_launch)]),
     "fpt_autotune": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int32, C.c_double,
@@ -321,6 +334,36 @@ def fpt_noise_table2(ctx: Context, model: int, kind: int, n_points: int, sigma: 
     _check(load().fpt_noise_table2(ctx.handle, model, kind, n_points, sigma, phi_lo, phi_hi,
                                    _ptr(uS), _ptr(out)), ctx.handle)
     return out[:n_points], out[n_points:2 * n_points], out[2 * n_points:]
+
+
+def fpt_power_spectrum(model, sigma: float, N_s, N_eval: float = NAN) -> np.ndarray:
+    Ns = np.ascontiguousarray(N_s, dtype=np.float64)
+    out = np.zeros(len(Ns))
+    m = model_struct(model)
+    _check(load().fpt_power_spectrum(C.byref(m), sigma, len(Ns), _ptr(Ns), N_eval, _ptr(out)))
+    return out
+
+
+def fpt_classical_dn(model, sigma: float = 1.0, n_k: int = 65, N_eval: float = NAN) -> dict:
+    m = model_struct(model)
+    o = fpt_classical()
+    _check(load().fpt_classical_dn(C.byref(m), sigma, n_k, N_eval, C.byref(o)))
+    return {k: getattr(o, k) for k, _ in fpt_classical._fields_}
+
+
+def fpt_classical_pdf(dN, sigma_R2: float, eps2: float) -> np.ndarray:
+    d = np.ascontiguousarray(dN, dtype=np.float64)
+    out = np.zeros(len(d))
+    _check(load().fpt_classical_pdf(_ptr(d), len(d), sigma_R2, eps2, _ptr(out)))
+    return out
+
+
+def fpt_fit_eps2(dN, pdf, se, sigma_R2: float, eps2_lo: float, eps2_hi: float) -> dict:
+    d, p, e = (np.ascontiguousarray(v, dtype=np.float64) for v in (dN, pdf, se))
+    eps2, chi2, used = C.c_double(), C.c_double(), C.c_int32()
+    _check(load().fpt_fit_eps2(_ptr(d), _ptr(p), _ptr(e), len(d), sigma_R2, eps2_lo, eps2_hi,
+                               C.byref(eps2), C.byref(chi2), C.byref(used)))
+    return dict(eps2=eps2.value, chi2=chi2.value, bins=used.value)
 
 
 def fpt_set_launch(ctx: Context, block: int = 0, blocks_per_sm: int = 0, check_steps: int = 0,
