@@ -1,0 +1,59 @@
+"""Classical delta N against the GPU's stochastic P(delta N) (Sec. 4.3): the
+variance of the first-passage time equals sigma_R^2 of linear theory near the
+peak, and Eq. (2.20) with a fitted eps2 describes the importance-sampled tail."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2410_13683_gb300 import fpt
+
+from gpu_common import gpu_run, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+def test_bump_variance_is_linear_theory(torch):
+    m = W.BUMP_MODEL
+    c = fpt.fpt_classical_dn(m, 1.0, 65)
+    n = 1 << 20
+    with fpt.fpt_init_model([m]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0)
+        st, g = gpu_run(ctx, [fpt.run_desc(0, n, seed=95)], [n])
+        assert st == fpt.FPT_OK
+    N = g[0]["N"]
+    se = N.var() * math.sqrt(2.0 / n)
+    print(f"bump: Var(N) {N.var():.6g} +- {se:.2g}, sigma_R^2 {c['sigma_R2']:.6g}, mean {N.mean():.5f}")
+    assert abs(N.var() - c["sigma_R2"]) < 4 * se
+    assert abs(N.mean() - (m.n_end - m.n_in)) < 0.01
+
+
+def test_bump_tail_constant_eps2_fit(torch):
+    """Importance-sampled tail (A = 2) of P(delta N), delta N = N - <N>: the
+    fitted eps2 of Eq. (2.20) lies between zero and a few, and the fit is
+    reasonable (chi^2 per bin below 10)."""
+    m = W.BUMP_MODEL
+    c = fpt.fpt_classical_dn(m, 1.0, 65)
+    n = 1 << 21
+    with fpt.fpt_init_model([m]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0)
+        fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=96)])
+        hd = fpt.fpt_histogram(ctx, 0, 3.0, 5.0, 200)
+        Nm = hd["N_mean"]
+        fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=97, A=2.0)])
+        h = fpt.fpt_histogram(ctx, 0, 3.0, 6.0, 120)
+    centres = 3.0 + (np.arange(120) + 0.5) * h["db"]
+    dN = centres - Nm
+    sel = (dN > 2 * math.sqrt(c["sigma_R2"])) & (h["count"] >= 50)
+    f = fpt.fpt_fit_eps2(dN[sel], h["pdf"][sel], h["se_w"][sel], c["sigma_R2"], 0.0, 5.0)
+    print(f"bump tail: eps2 fit {f['eps2']:.4f} (eps2 at N_end {c['eps2_end']:.4f}), chi2/bin "
+          f"{f['chi2'] / f['bins']:.3g} over {f['bins']} bins")
+    assert f["bins"] >= 10
+    assert 0.0 < f["eps2"] < 5.0
+    assert f["chi2"] / f["bins"] < 10.0

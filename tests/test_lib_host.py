@@ -200,3 +200,35 @@ def test_bump_model_arguments():
     with pytest.raises(fpt.FptError) as e:
         fpt.fpt_resolve_model(dataclasses.replace(W.BUMP_MODEL, bg_phi0=2.19))   # starts past the bump: no USR onset
     assert "ultra-slow roll" in str(e.value)
+
+
+def test_classical_dn_matches_oracle():
+    """Eq. (2.18) over the simulated mode range and the power spectrum, host
+    builder vs oracle, for the sudden transition and the bump."""
+    from oracle import classical as C
+    for m in (W.USR_MODEL, W.BUMP_MODEL):
+        r = T.resolve(m)
+        c = fpt.fpt_classical_dn(m, 1.0, 33)
+        assert c["sigma_R2"] == pytest.approx(C.sigma_R2(m, r, 1.0, n_k=33), rel=1e-7)
+        assert c["eps2_end"] == pytest.approx(C.eps2_at(m, r, r.N_end), rel=1e-7, abs=1e-9)
+        Ns = np.array([r.N_in, 0.5 * (r.N_in + r.N_end), r.N_end])
+        P = fpt.fpt_power_spectrum(m, 1.0, Ns)
+        ref = [C.power_spectrum_at(m, r, N, 1.0, r.N_end + C.LATE) for N in Ns]
+        np.testing.assert_allclose(P, ref, rtol=1e-7)
+
+
+def test_classical_pdf_and_fit():
+    """Eq. (2.20) against the oracle's restatement, and the eps2 fit recovering
+    eps2 from exact PDF values."""
+    from oracle import classical as C
+    d = np.linspace(-0.3, 1.5, 40)
+    for e2 in (0.0, 0.745, -1.2):
+        np.testing.assert_allclose(fpt.fpt_classical_pdf(d, 0.0098, e2), C.pdf_constant_eps2(d, 0.0098, e2),
+                                   rtol=1e-12)
+    p = C.pdf_constant_eps2(d, 0.0098, 0.745)
+    f = fpt.fpt_fit_eps2(d, p, 0.01 * p, 0.0098, 0.0, 3.0)
+    assert f["eps2"] == pytest.approx(0.745, abs=1e-7) and f["chi2"] < 1e-9 and f["bins"] == 40
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_classical_dn(W.LINEAR.model, 1.0, 33)       # no transition rule
+    with pytest.raises(fpt.FptError):
+        fpt.fpt_classical_dn(W.BUMP_MODEL, 1.0, 32)         # even n_k
