@@ -52,7 +52,11 @@ def test_2d_usr_parity(torch, usr_numeric, betas):
     for r, (b1, b2) in enumerate(betas):
         o = OS.run2(m, res, tab, seed=80, run_id=r, n=n, A=b1, A2=b2)
         o.phi_end_value = res.phi_end
-        mism, near = compare(g[r], o, res.phi_in - res.phi_end, f"2-D usr beta=({b1},{b2})")
+        # The matched noise changes by x4 across [phi_end, phi_in], so a field
+        # error grows multiplicatively along a path; FP32 and FP64 paths longer
+        # than 4x the median (20000 steps) are compared in law.
+        mism, near = compare(g[r], o, res.phi_in - res.phi_end, f"2-D usr beta=({b1},{b2})",
+                             pathwise_max_steps=20000)
         print(f"2-D usr beta=({b1},{b2}): mismatch {mism:.4%}, near-ties {near:.4%}")
         if b1 or b2:
             assert np.std(o.logw) > 0.1
