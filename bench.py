@@ -62,6 +62,10 @@ INSTR_PER_STEP_MLP = 66
 # drift 9, (phi, pi) update 8, field compensated add 4, log-weight (Kahan) 7,
 # counter + passage 5, predication 2.
 INSTR_PER_STEP_2D = 87
+# Bump stepper: the plain step with the drift from the cubic table (index 5,
+# Horner 3, load 1) instead of the closed form (6), and the compensated
+# momentum (+3).
+INSTR_PER_STEP_BUMP = 66
 # Training recipe of the learned proposal (log-variance loss towards
 # e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum).
 TRAIN = dict(rounds=300, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4)
@@ -285,6 +289,66 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     return out
 
 
+def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max):
+    """Gaussian-bump model (Sec. 4.3), 4096-point Bessel table at sigma = 1:
+    direct-sampling throughput of the stepper with the tabulated drift, and the
+    classical-delta-N comparison -- Var(N) of the direct run against
+    sigma_R^2 of linear theory (Eq. 2.18), and the eps2 of Eq. (2.20) fitted
+    to the importance-sampled tail (A = 2) against eps2 at the end of the
+    mode range."""
+    m = W.BUMP_MODEL
+    nd = 1 << 22
+    out = {"model": "Gaussian bump, K=1.17e-3 m=0.5 width=1.59e-2 phi0=2.18812, V0 from P_R peak 5e-3",
+           "n_traj_per_run": nd}
+    t0 = time.perf_counter()
+    c = fpt.fpt_classical_dn(m, 1.0, 129)
+    out["classical_host_s"] = round(time.perf_counter() - t0, 3)
+    ctx = fpt.fpt_init_model([m], device=torch.cuda.current_device())
+    fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0)
+    fpt.fpt_autotune(ctx, [fpt.run_desc(0, nd, seed=seed + 9, run_id=99)], fraction=0.25)
+    d = lambda k, A=0.0: fpt.run_desc(0, nd, seed=seed + 9, run_id=k, A=A, traj_offset=rank * nd)
+    fpt.fpt_run(ctx, [d(100)], stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, steps = [], 0.0
+    for k in range(3):
+        e0.record(stream)
+        fpt.fpt_run(ctx, [d(k)], stream=stream)
+        e1.record(stream)
+        h = fpt.fpt_histogram(ctx, 0, 3.0, 5.0, 200, stream=stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        steps += h["N_mean"] * h["n_passed"] / m.dN
+    t = sum(ms) * 1e-3
+    out["direct_traj_per_s"] = 3 * nd / t
+    out["em_steps_per_s"] = steps / t
+    rl = roofline(steps / 3, float(np.mean(ms)), sm_count, sm_max, None, INSTR_PER_STEP_BUMP)
+    rl["kernel"] = "em_kernel<direct, smem table, drift table>"
+    out["roofline"] = rl
+    Nbuf = np.zeros(nd)
+    fpt.fpt_run(ctx, [d(3)], [dict(N=Nbuf)], stream=stream)
+    fpt.fpt_sync(ctx)
+    varN = float(Nbuf.var())
+    out["classical_dn"] = {"sigma_R2": c["sigma_R2"], "var_N": varN,
+                           "var_N_se": varN * math.sqrt(2.0 / nd), "mean_N": float(Nbuf.mean()),
+                           "eps2_end": c["eps2_end"]}
+    Nm = float(Nbuf.mean())
+    fpt.fpt_run(ctx, [d(7, 2.0)], stream=stream)
+    hb = fpt.fpt_histogram(ctx, 0, 3.0, 6.0, 120, stream=stream)
+    centres = 3.0 + (np.arange(120) + 0.5) * hb["db"]
+    dN = centres - Nm
+    sel = (dN > 2 * math.sqrt(c["sigma_R2"])) & (hb["count"] >= 50)
+    if sel.sum() >= 5:
+        f = fpt.fpt_fit_eps2(dN[sel], hb["pdf"][sel], hb["se_w"][sel], c["sigma_R2"], 0.0, 5.0)
+        out["classical_dn"].update({"eps2_fit": f["eps2"], "fit_chi2_per_bin": f["chi2"] / f["bins"],
+                                    "fit_bins": f["bins"], "fit_range_dN": [float(dN[sel].min()),
+                                                                            float(dN[sel].max())]})
+        gauss = fpt.fpt_classical_pdf(dN[sel], c["sigma_R2"], 0.0)
+        out["classical_dn"]["tail_over_gaussian_max"] = float(np.max(hb["pdf"][sel] / gauss))
+    fpt.fpt_sync(ctx)
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +364,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / judge / direct legs")
     ap.add_argument("--no-2d", action="store_true", help="skip the full-rank (2-D) noise leg")
+    ap.add_argument("--no-bump", action="store_true", help="skip the Gaussian-bump leg")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -452,6 +517,9 @@ def main():
             sm_max_2d = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
             extras["noise_2d"] = noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
                                               sm_count, sm_max_2d)
+        if not args.no_bump:
+            sm_max_b = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+            extras["bump"] = bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max_b)
 
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
