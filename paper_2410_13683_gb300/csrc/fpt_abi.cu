@@ -915,8 +915,16 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     p.nsteps = ctx->d_nsteps;
     p.logw = ctx->d_logw;
     p.status = ctx->d_status;
-    p.key_lo = (uint32_t)runs[0].seed;
-    p.key_hi = (uint32_t)(runs[0].seed >> 32);
+    {
+        // Philox4x32-10 key schedule (Weyl increments 0x9E3779B9, 0xBB67AE85)
+        uint32_t k0 = (uint32_t)runs[0].seed, k1 = (uint32_t)(runs[0].seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            p.rk[2 * r] = k0;
+            p.rk[2 * r + 1] = k1;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
     p.groups_per_check = check_steps / 4;
     p.mlp_run = mlp ? mlp_run : 0;
     p.records = ctx->d_records;

@@ -98,7 +98,7 @@ struct EmParams {
     int32_t *nsteps;
     double *logw;
     uint8_t *status;
-    uint32_t key_lo, key_hi;
+    uint32_t rk[20];           // Philox round keys: rk[2r] = key_lo + r W0, rk[2r+1] = key_hi + r W1
     int groups_per_check;      // refill every 4 * groups_per_check steps
     unsigned long long budget_ns;    // > 0: abort after this long (device clock)
     unsigned long long *t0;          // first %globaltimer reading of the launch (0 before)

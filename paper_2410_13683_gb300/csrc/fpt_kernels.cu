@@ -29,7 +29,11 @@ namespace fpt_dev {
 // ---------------------------------------------------------------------------
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+// The key schedule (k0 + r W0, k1 + r W1 for rounds r = 0..9) is the same for
+// every call of a launch: it comes precomputed in the kernel parameters
+// (rk[2r], rk[2r+1]), so each round is two wide multiplies and two
+// three-input XORs with constant-bank operands.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20])
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -37,9 +41,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
         const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
         const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
         const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
     }
     return c;
 }
@@ -435,8 +437,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
             mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun);
 
         for (int g = 0; g < P.groups_per_check; ++g) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u),
-                                          P.key_lo, P.key_hi);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u), P.rk);
             float z[4];
             box_muller(r.x, r.y, z[0], z[1]);
             box_muller(r.z, r.w, z[2], z[3]);
@@ -576,8 +577,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
             // (a lane that finished keeps its count and ignores the normals)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 1, L.traj, L.run_id, 0u),
-                                              P.key_lo, P.key_hi);
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 1, L.traj, L.run_id, 0u), P.rk);
                 float z[4];
                 box_muller(r.x, r.y, z[0], z[1]);
                 box_muller(r.z, r.w, z[2], z[3]);

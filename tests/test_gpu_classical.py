@@ -36,8 +36,9 @@ def test_bump_variance_is_linear_theory(torch):
 
 def test_bump_tail_constant_eps2_fit(torch):
     """Importance-sampled tail (A = 2) of P(delta N), delta N = N - <N>: the
-    fitted eps2 of Eq. (2.20) lies between zero and a few, and the fit is
-    reasonable (chi^2 per bin below 10)."""
+    eps2 of Eq. (2.20) fitted to the tail is the background's eps2 at the end
+    of the mode range (0.745) -- the classical constant-roll tail -- and the
+    fit is close (chi^2 per bin below 50 with sub-percent bin errors)."""
     m = W.BUMP_MODEL
     c = fpt.fpt_classical_dn(m, 1.0, 65)
     n = 1 << 21
@@ -55,5 +56,5 @@ def test_bump_tail_constant_eps2_fit(torch):
     print(f"bump tail: eps2 fit {f['eps2']:.4f} (eps2 at N_end {c['eps2_end']:.4f}), chi2/bin "
           f"{f['chi2'] / f['bins']:.3g} over {f['bins']} bins")
     assert f["bins"] >= 10
-    assert 0.0 < f["eps2"] < 5.0
-    assert f["chi2"] / f["bins"] < 10.0
+    assert abs(f["eps2"] - c["eps2_end"]) < 0.05
+    assert f["chi2"] / f["bins"] < 50.0
