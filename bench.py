@@ -225,7 +225,7 @@ def peak_pdf(fpt, ctx, run, stream, N_lo, N_hi, bins=48):
     return np.asarray(h["pdf"]), np.asarray(h["se_jk"]), h["N_mean"]
 
 
-def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm_max):
+def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm_max, autotune=True):
     """Full-rank noise (numerical matching of Eq. 3.9 at sigma = 1, 4096
     points) on the same model: direct-sampling throughput of the 2-D stepper,
     its issue roofline, the tail ESS rate with the constant standardised bias
@@ -238,7 +238,8 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     fpt.fpt_noise_table2(ctx2, 0, fpt.FPT_TABLE_NUMERIC, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
     out["table_build_s"] = round(time.perf_counter() - t0, 3)
     fpt.fpt_noise_table(ctx2, 1, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
-    fpt.fpt_autotune(ctx2, [fpt.run_desc(0, nd, seed=seed + 5, run_id=99)], fraction=0.25)
+    if autotune:
+        fpt.fpt_autotune(ctx2, [fpt.run_desc(0, nd, seed=seed + 5, run_id=99)], fraction=0.25)
     d2 = lambda k, A_=0.0: fpt.run_desc(0, nd, seed=seed + 5, run_id=k, A=A_, traj_offset=rank * nd)
     fpt.fpt_run(ctx2, [d2(100)], stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -289,7 +290,7 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     return out
 
 
-def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max):
+def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max, autotune=True):
     """Gaussian-bump model (Sec. 4.3), 4096-point Bessel table at sigma = 1:
     direct-sampling throughput of the stepper with the tabulated drift, and the
     classical-delta-N comparison -- Var(N) of the direct run against
@@ -305,7 +306,8 @@ def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max):
     out["classical_host_s"] = round(time.perf_counter() - t0, 3)
     ctx = fpt.fpt_init_model([m], device=torch.cuda.current_device())
     fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0)
-    fpt.fpt_autotune(ctx, [fpt.run_desc(0, nd, seed=seed + 9, run_id=99)], fraction=0.25)
+    if autotune:
+        fpt.fpt_autotune(ctx, [fpt.run_desc(0, nd, seed=seed + 9, run_id=99)], fraction=0.25)
     d = lambda k, A=0.0: fpt.run_desc(0, nd, seed=seed + 9, run_id=k, A=A, traj_offset=rank * nd)
     fpt.fpt_run(ctx, [d(100)], stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -516,10 +518,11 @@ def main():
         if not args.no_2d:
             sm_max_2d = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
             extras["noise_2d"] = noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
-                                              sm_count, sm_max_2d)
+                                              sm_count, sm_max_2d, autotune=not args.no_autotune)
         if not args.no_bump:
             sm_max_b = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-            extras["bump"] = bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max_b)
+            extras["bump"] = bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max_b,
+                                      autotune=not args.no_autotune)
 
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
