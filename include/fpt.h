@@ -412,6 +412,12 @@ fpt_status fpt_mlp_grad(fpt_ctx *ctx, const float *params, const float *s, const
                         const float *dalpha, int64_t n, float alpha_max, float *grad,
                         void *cuda_stream);
 
+/* Full-rank (2-D) counterpart: grad = sum_r dbeta_r . dbeta(s_r)/dtheta with
+ * beta = (clamp(o1), clamp(o2)) (each to +-alpha_max, zero gradient on a
+ * clamped component); dbeta n x 2 (host or device). Blocks until done. */
+fpt_status fpt_mlp_grad2(fpt_ctx *ctx, const float *params, const float *s, const float *dbeta, int64_t n,
+                         float alpha_max, float *grad, void *cuda_stream);
+
 typedef struct {
     float lr, beta1, beta2, eps;
     float clip;            /* > 0: clamp each gradient component first        */
@@ -435,6 +441,7 @@ typedef struct {
  * L = Var[ln w + lambda min(N, N_cut)] at the sampling parameters,
  *   dL/dtheta = (2/n) sum_j (Y_j - mean_chunk Y) d ln w_j / dtheta,
  *   d ln w_j / dtheta = -sum_s sqrt(dN) (sum of xi over segment s) d alpha_s / dtheta,
+ * (on a 2-D table: -sum_s sqrt(dN) sum_k (sum of xi_k over s) d beta_{s,k} / dtheta)
  * is accumulated, one Adam step updates params / adam_m / adam_v (device,
  * FPT_MLP_PARAMS floats each) and the blob is re-packed. Returns
  * FPT_E_NOMEM if a chunk's segment records exceed the record buffer (use a

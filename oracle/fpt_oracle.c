@@ -347,11 +347,21 @@ static double clampd(double v, double lim)
     return v > lim ? lim : (v < -lim ? -lim : v);
 }
 
+/* Optional per-segment record of the learned 2-D bias. */
+typedef struct {
+    int64_t cap;
+    int64_t *n_seg;
+    double *state;       /* [cap][3] (x or ln x, pi, N) at the segment start */
+    double *beta;        /* [cap][2] beta used */
+    double *sum_xi;      /* [cap][2] sums of xi_1, xi_2 over the segment */
+} oracle_segments2;
+
 static void one_trajectory2(const oracle_model *m, const oracle_table2 *tab, const oracle_bias *bias,
                             double A2, uint64_t seed, uint32_t run_id, uint32_t traj,
                             int64_t *nsteps, double *logw, uint8_t *status, double *phi_f,
-                            double *pi_f, double *xmin)
+                            double *pi_f, double *xmin, oracle_segments2 *seg)
 {
+    int64_t ns = 0;
     const double dN = m->dN, sdN = sqrt(m->dN);
     double phi = m->phi_in, pi = m->pi_in, lw = 0.0, xm = INFINITY;
     double beta1 = 0.0, beta2 = 0.0;
@@ -372,6 +382,17 @@ static void one_trajectory2(const oracle_model *m, const oracle_table2 *tab, con
             oracle_mlp_forward(bias, s, o);
             beta1 = clampd(o[0], bias->alpha_max);
             beta2 = clampd(o[1], bias->alpha_max);
+            if (seg && ns < seg->cap) {
+                for (int k = 0; k < 3; ++k) seg->state[3 * ns + k] = s[k];
+                seg->beta[2 * ns] = beta1;
+                seg->beta[2 * ns + 1] = beta2;
+                seg->sum_xi[2 * ns] = seg->sum_xi[2 * ns + 1] = 0.0;
+            }
+            ++ns;
+        }
+        if (bias->kind == 2 && seg && ns - 1 < seg->cap) {
+            seg->sum_xi[2 * (ns - 1)] += xi1;
+            seg->sum_xi[2 * (ns - 1) + 1] += xi2;
         }
         double B_phi = a * beta1 + b * beta2, B_pi = b * beta1 + c * beta2;   /* B = S beta */
         double drift_pi = -(3.0 - 0.5 * pi * pi) * (pi + dlnV(m, phi));
@@ -391,6 +412,18 @@ static void one_trajectory2(const oracle_model *m, const oracle_table2 *tab, con
     *phi_f = phi;
     *pi_f = pi;
     *xmin = xm;
+    if (seg) *seg->n_seg = ns < seg->cap ? ns : seg->cap;
+}
+
+/* One learned-bias 2-D trajectory with its per-segment records. */
+int oracle_run2_segments(const oracle_model *m, const oracle_table2 *tab, const oracle_bias *bias,
+                         uint64_t seed, uint32_t run_id, uint32_t traj, int64_t *nsteps, double *logw,
+                         uint8_t *status, oracle_segments2 *seg)
+{
+    if (!m || !tab || !bias || !seg || bias->kind != 2 || bias->segment < 1) return 1;
+    double phi_f, pi_f, xm;
+    one_trajectory2(m, tab, bias, 0.0, seed, run_id, traj, nsteps, logw, status, &phi_f, &pi_f, &xm, seg);
+    return 0;
 }
 
 int oracle_run2(const oracle_model *m, const oracle_table2 *tab, const oracle_bias *bias, double A2,
@@ -406,7 +439,7 @@ int oracle_run2(const oracle_model *m, const oracle_table2 *tab, const oracle_bi
     for (int64_t i = 0; i < n; ++i) {
         one_trajectory2(m, tab, bias, A2, seed, run_id, (uint32_t)(traj0 + i), &out->nsteps[i],
                         &out->logw[i], &out->status[i], &out->phi_final[i], &out->pi_final[i],
-                        &out->xmin_pre[i]);
+                        &out->xmin_pre[i], NULL);
     }
     return 0;
 }

@@ -20,6 +20,13 @@ ln w_theta = -sum_s [alpha_s zeta_s - alpha_s^2 m_s dN / 2], zeta_s the
 standardised increment of segment s (m_s steps); at the sampling parameters
 d ln w / d theta = -sum_s sqrt(dN) (sum of xi over s) d alpha_s / d theta, so
 dL/dtheta = (2/n) sum_j (Y_j - mean Y) d ln w_j / d theta, Y = ln w + lambda N.
+
+Full-rank (2-D) noise: the bias is B = S beta with beta = (clamp o1, clamp o2)
+(each to +-alpha_max, held per segment), the weight increment of Eq. (4.5) is
+beta . (beta dN/2 + xi sqrt(dN)), so ln w_theta = -sum_s [beta_s . zeta_s -
+|beta_s|^2 m_s dN / 2] with zeta_s the sums of the standardised increments, and
+at the sampling parameters d ln w / d theta = -sum_s sqrt(dN) sum_k
+(sum of xi_k over s) d beta_{s,k} / d theta.
 """
 from __future__ import annotations
 
@@ -135,3 +142,45 @@ def logw_at(p, tr, dN, shift, scale, alpha_max, segment, round_bf16=False):
     o, _ = forward(p, normalise(tr["state"], shift, scale), round_bf16)
     a = alpha_of(o, tr["tan_theta"], alpha_max)
     return float(-np.sum(a * zeta - 0.5 * a * a * m * dN))
+
+
+def beta_of(o, alpha_max):
+    """2-D bias: each network output clamped to +-alpha_max."""
+    return np.clip(o, -alpha_max, alpha_max)
+
+
+def beta_grad(p, s, alpha_max, dbeta, round_bf16=False):
+    """Gradient of sum(dbeta * beta(s)) with respect to the parameters
+    (zero on a clamped component)."""
+    o, cache = forward(p, s, round_bf16)
+    do = np.where(np.abs(o) < alpha_max, dbeta, 0.0)
+    return backward(p, cache, do)
+
+
+def logvar_loss_grad2(p, trajs, dN, lam, shift, scale, alpha_max, round_bf16=False):
+    """Log-variance loss and gradient for 2-D paths (oracle.stepper.run2_segments)."""
+    Y = np.array([tr["logw"] + lam * tr["nsteps"] * dN for tr in trajs])
+    n = len(trajs)
+    Ybar = Y.mean()
+    loss = float(np.mean((Y - Ybar) ** 2))
+    grads = {k: np.zeros_like(p[k]) for k in KEYS}
+    for j, tr in enumerate(trajs):
+        if len(tr["sum_xi"]) == 0:
+            continue
+        coef = 2.0 / n * (Y[j] - Ybar)
+        dbeta = coef * (-np.sqrt(dN) * tr["sum_xi"])
+        g = beta_grad(p, normalise(tr["state"], shift, scale), alpha_max, dbeta, round_bf16)
+        for k in KEYS:
+            grads[k] += g[k]
+    return loss, grads
+
+
+def logw_at2(p, tr, dN, shift, scale, alpha_max, segment, round_bf16=False):
+    """ln w_theta of a recorded 2-D path under parameters p (off-policy)."""
+    k = len(tr["sum_xi"])
+    m = np.full(k, float(segment))
+    m[-1] = tr["nsteps"] - segment * (k - 1)
+    zeta = np.sqrt(dN) * tr["sum_xi"] + tr["beta"] * (m * dN)[:, None]
+    o, _ = forward(p, normalise(tr["state"], shift, scale), round_bf16)
+    b = beta_of(o, alpha_max)
+    return float(-np.sum(b * zeta) + 0.5 * np.sum(b * b * (m * dN)[:, None]))

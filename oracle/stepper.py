@@ -59,6 +59,11 @@ class _Table2(C.Structure):
                 ("Sqq", C.POINTER(C.c_double))]
 
 
+class _Seg2(C.Structure):
+    _fields_ = [("cap", C.c_int64), ("n_seg", C.POINTER(C.c_int64)), ("state", C.POINTER(C.c_double)),
+                ("beta", C.POINTER(C.c_double)), ("sum_xi", C.POINTER(C.c_double))]
+
+
 class _Out(C.Structure):
     _fields_ = [("nsteps", C.POINTER(C.c_int64)), ("logw", C.POINTER(C.c_double)),
                 ("status", C.POINTER(C.c_uint8)), ("phi_final", C.POINTER(C.c_double)),
@@ -95,6 +100,10 @@ def lib():
                                      C.c_double, C.c_uint64, C.c_uint32, C.c_int64, C.c_int64,
                                      C.c_int, C.POINTER(_Out)]
         _lib.oracle_run2.restype = C.c_int
+        _lib.oracle_run2_segments.argtypes = [C.POINTER(_Model), C.POINTER(_Table2), C.POINTER(_Bias),
+                                              C.c_uint64, C.c_uint32, C.c_uint32, C.POINTER(C.c_int64),
+                                              C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.POINTER(_Seg2)]
+        _lib.oracle_run2_segments.restype = C.c_int
         _lib.oracle_mlp_forward.argtypes = [C.POINTER(_Bias), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
         _lib.oracle_max_threads.restype = C.c_int
@@ -253,3 +262,24 @@ def run2(m, resolved, table2, seed: int, run_id: int, n: int, traj0: int = 0, A:
     if rc != 0:
         raise ValueError("oracle_run2 rejected its arguments")
     return Trajectories(dN=m.dN, **out)
+
+
+def run2_segments(m, resolved, table2, mlp: MLPBias, seed: int, run_id: int, traj: int, cap: int = 1 << 16):
+    """One learned-bias 2-D trajectory with its per-segment records (state,
+    beta, sums of xi_1 and xi_2)."""
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (table2.Spp, table2.Spq, table2.Sqq)]
+    tab = _Table2(n_points=len(arrs[0]), phi_lo=table2.phi_lo, h=table2.h, Spp=_dp(arrs[0]),
+                  Spq=_dp(arrs[1]), Sqq=_dp(arrs[2]))
+    ms = model_struct(m, resolved.phi_in, resolved.pi_in, resolved.phi_end)
+    b = mlp.struct()
+    n_seg = C.c_int64(0)
+    state = np.zeros((cap, 3)); beta = np.zeros((cap, 2)); sx = np.zeros((cap, 2))
+    seg = _Seg2(cap=cap, n_seg=C.pointer(n_seg), state=_dp(state), beta=_dp(beta), sum_xi=_dp(sx))
+    ns = C.c_int64(0); lw = C.c_double(0.0); st = C.c_uint8(0)
+    rc = lib().oracle_run2_segments(C.byref(ms), C.byref(tab), C.byref(b), seed, run_id, traj,
+                                    C.byref(ns), C.byref(lw), C.byref(st), C.byref(seg))
+    if rc != 0:
+        raise ValueError("oracle_run2_segments rejected its arguments")
+    k = n_seg.value
+    return dict(nsteps=ns.value, logw=lw.value, status=st.value, state=state[:k], beta=beta[:k],
+                sum_xi=sx[:k])

@@ -886,8 +886,6 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const bool smem = used_models.size() == 1;
     const int smem_model = smem ? *used_models.begin() : 0;
     const bool mlp = mlp_run >= 0;
-    if (mlp && ctx->record_mode && rank2 == 1)
-        return fail(ctx, FPT_E_INVALID, "training records need a 1-D noise table");
     const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
     const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
@@ -1270,6 +1268,35 @@ fpt_status fpt_mlp_grad(fpt_ctx *ctx, const float *params, const float *s_in, co
     return FPT_OK;
 }
 
+fpt_status fpt_mlp_grad2(fpt_ctx *ctx, const float *params, const float *s_in, const float *dbeta, int64_t n,
+                         float alpha_max, float *grad, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!params || !s_in || !dbeta || !grad || n < 1) return fail(ctx, FPT_E_INVALID, "null buffer or n < 1");
+    if (!(alpha_max > 0.0f)) return fail(ctx, FPT_E_INVALID, "alpha_max must be positive");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    // records (in0, in1, in2, -, ...) and the direct output gradients, built on the host
+    std::vector<float> hs(3 * n), hd(2 * n), hrec(8 * n, 0.0f), hp(kMlpParams);
+    CK(cudaMemcpy(hs.data(), s_in, sizeof(float) * 3 * n, cudaMemcpyDefault));
+    CK(cudaMemcpy(hd.data(), dbeta, sizeof(float) * 2 * n, cudaMemcpyDefault));
+    CK(cudaMemcpy(hp.data(), params, sizeof(float) * kMlpParams, cudaMemcpyDefault));
+    for (int64_t i = 0; i < n; ++i) {
+        hrec[8 * i] = hs[3 * i]; hrec[8 * i + 1] = hs[3 * i + 1]; hrec[8 * i + 2] = hs[3 * i + 2];
+    }
+    fpt_status st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, 10 * n + 2 * kMlpParams);
+    if (st != FPT_OK) return st;
+    float *drec = ctx->d_tmp, *dd = drec + 8 * n, *dp = dd + 2 * n, *dg = dp + kMlpParams;
+    CK(cudaMemcpyAsync(drec, hrec.data(), sizeof(float) * 8 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dd, hd.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dp, hp.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dg, 0, sizeof(float) * kMlpParams, s));
+    CK(mlp_bwd_launch(dp, drec, n, nullptr, 0.0f, alpha_max, dd, dg, ctx->sm_count, s, 1));
+    CK(cudaMemcpyAsync(grad, dg, sizeof(float) * kMlpParams, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return FPT_OK;
+}
+
 fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t chunk, double lambda,
                                double N_cut, const fpt_adam *adam, float *params, float *adam_m,
                                float *adam_v, void *blob, fpt_train_stats *stats, void *cuda_stream)
@@ -1327,7 +1354,7 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
         CK(mlp_coef_launch(ctx->d_nsteps, ctx->d_logw, sub.n_traj, m.dN, lambda, N_cut, 2.0 / (double)n_total,
                            ctx->d_Y, ctx->d_acc, ctx->d_coef, s));
         CK(mlp_bwd_launch(params, ctx->d_records, (long long)n_rec, ctx->d_coef, (float)m.dN, run->alpha_max,
-                          nullptr, ctx->d_grad, ctx->sm_count, s));
+                          nullptr, ctx->d_grad, ctx->sm_count, s, ctx->tables[run->model].rank2 ? 1 : 0));
         double acc[2];
         CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
         // mean first-passage time of the chunk

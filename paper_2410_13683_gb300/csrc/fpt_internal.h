@@ -151,7 +151,8 @@ cudaError_t mlp_eval_launch(const void *blob, const float *s, const float *tan_t
 cudaError_t mlp_coef_launch(const int32_t *nsteps, const double *logw, long long n, double dN, double lambda,
                             double N_cut, double scale, double *Y, double *acc, float *coef, cudaStream_t s);
 cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_rec, const float *coef, float dN,
-                           float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s);
+                           float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s,
+                           int rank2 = 0);
 cudaError_t mlp_adam_launch(float *P, const float *G, float *m, float *v, int n, float lr, float b1, float b2,
                             float eps, int step, float clip, cudaStream_t s);
 size_t mlp_bwd_smem();

@@ -120,6 +120,7 @@ struct Lane {                // per-thread trajectory state and its constants
 
 struct SegRec {              // open segment of the record variant
     float in0, in1, in2, tan_t, raw, sum_xi;
+    float sum_xi2;           // 2-D noise: sum of xi_2 (sum_xi holds xi_1)
     int n0;
     bool open;
 };
@@ -405,6 +406,35 @@ __device__ __forceinline__ bool past_deadline(const EmParams &P, unsigned long l
     return __shfl_sync(0xffffffffu, stop, 0) != 0;
 }
 
+// Close the warp's open segments at a refill point: record r holds
+// q0 = (inputs, slot 3) and q1 = (slot 4, slot 5, unit, steps), appended with
+// one warp-aggregated atomic on the record cursor; records past the buffer
+// raise flag 3 instead of being written.
+__device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, SegRec &sg, bool active,
+                                              float4 q0, float s4, float s5)
+{
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const bool wr = active && sg.open;
+    const unsigned m = __ballot_sync(FULL, wr);
+    if (m) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.rec_cursor, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (wr) {
+            const long long idx = (long long)(base + __popc(m & ((1u << lane) - 1u)));
+            if (idx < P.rec_cap) {
+                float4 *q = reinterpret_cast<float4 *>(P.records + 8 * idx);
+                q[0] = q0;
+                q[1] = make_float4(s4, s5, __uint_as_float((uint32_t)L.unit), __int_as_float(L.n - sg.n0));
+            } else {
+                atomicExch(P.flags + 3, 1);
+            }
+        }
+    }
+    sg.open = false;
+}
+
 // Register budgets: the plain stepper keeps three 512-thread blocks per SM
 // (48 warps); the learned-proposal stepper at most 384 threads per block and
 // two resident blocks, so that the network's registers still leave 24 warps.
@@ -451,25 +481,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
 
         if (REC) {
             // close the segments of this interval: (inputs, tan, raw alpha, sum xi, unit, steps)
-            const bool wr = active && sg.open;
-            const unsigned m = __ballot_sync(FULL, wr);
-            if (m) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(P.rec_cursor, (unsigned long long)__popc(m));
-                base = __shfl_sync(FULL, base, 0);
-                if (wr) {
-                    const long long idx = (long long)(base + __popc(m & ((1u << lane) - 1u)));
-                    if (idx < P.rec_cap) {
-                        float4 *q = reinterpret_cast<float4 *>(P.records + 8 * idx);
-                        q[0] = make_float4(sg.in0, sg.in1, sg.in2, sg.tan_t);
-                        q[1] = make_float4(sg.raw, sg.sum_xi, __uint_as_float((uint32_t)L.unit),
-                                           __int_as_float(L.n - sg.n0));
-                    } else {
-                        atomicExch(P.flags + 3, 1);
-                    }
-                }
-            }
-            sg.open = false;
+            write_records(P, L, sg, active, make_float4(sg.in0, sg.in1, sg.in2, sg.tan_t), sg.raw, sg.sum_xi);
         }
 
         // refill point: write finished trajectories, fetch new work
@@ -527,7 +539,8 @@ __device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const floa
 }
 
 // Learned proposal in 2-D: beta = (clamp(o1), clamp(o2)) at the segment start.
-__device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, const uint2 *tiles,
+template <bool REC>
+__device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, SegRec &sg, const uint2 *tiles,
                                                    const float *bias, const RunDev &pr)
 {
     float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f;
@@ -546,10 +559,17 @@ __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, const uin
         L.cb = b1 * L.sqrt_dN;
         L.cb_b = b2 * L.sqrt_dN;
         L.half_cb2 = 0.5f * fmaf(b1, b1, b2 * b2) * L.dN;
+        if (REC) {
+            sg.in0 = in0; sg.in1 = in1; sg.in2 = in2;
+            sg.sum_xi = 0.0f;
+            sg.sum_xi2 = 0.0f;
+            sg.n0 = L.n;
+            sg.open = true;
+        }
     }
 }
 
-template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB>
+template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB, bool REC = false>
 __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
@@ -565,12 +585,14 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
     const float4 *tab = SMEM ? s_tab : P.tables;
     const unsigned FULL = 0xffffffffu;
     Lane L;
+    SegRec sg;
+    sg.open = false;
     bool active = false, done = false;
     first_units(P, L, active, s_run, s_model);
 
     for (;;) {
         if (MLP && __any_sync(FULL, active && L.mlp))
-            mlp2_segment_start(L, active && L.mlp, s_tiles, s_bias, prun);
+            mlp2_segment_start<REC>(L, active && L.mlp, sg, s_tiles, s_bias, prun);
 
         for (int g = 0; g < P.groups_per_check; ++g) {
             // four steps per group, two per Philox block: L.n is even at each block
@@ -581,10 +603,18 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
                 float z[4];
                 box_muller(r.x, r.y, z[0], z[1]);
                 box_muller(r.z, r.w, z[2], z[3]);
-                if (active && !done) done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model);
-                if (active && !done) done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model);
+                if (active && !done) {
+                    if (REC) { sg.sum_xi += z[0]; sg.sum_xi2 += z[1]; }
+                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model);
+                }
+                if (active && !done) {
+                    if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
+                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model);
+                }
             }
         }
+        // 2-D records: (inputs, sum xi_2), (0, sum xi_1, unit, steps)
+        if (REC) write_records(P, L, sg, active, make_float4(sg.in0, sg.in1, sg.in2, sg.sum_xi2), 0.0f, sg.sum_xi);
         refill_point(P, L, active, done, s_run, s_model);
         if (!__any_sync(FULL, active)) break;
         if (P.budget_ns && past_deadline(P, s_t0)) break;
@@ -595,6 +625,8 @@ template <bool DTAB>
 static const void *em_fn_t(EmVariant v)
 {
     if (v.rank2) {
+        if (v.rec) return v.smem ? (const void *)em2_kernel<true, true, true, DTAB, true>
+                                 : (const void *)em2_kernel<true, false, true, DTAB, true>;
         if (v.mlp) return v.smem ? (const void *)em2_kernel<true, true, true, DTAB>
                                  : (const void *)em2_kernel<true, false, true, DTAB>;
         if (v.weighted) return v.smem ? (const void *)em2_kernel<true, true, false, DTAB>

@@ -149,6 +149,9 @@ cudaError_t mlp_coef_launch(const int32_t *nsteps, const double *logw, long long
 // ---------------------------------------------------------------------------
 // Record layout (8 x 32-bit): in0, in1, in2, tan_t, raw alpha, sum_xi, unit, steps.
 // dalpha = coef[unit] * (-sqrt(dN) * sum_xi), zero where |raw alpha| >= amax.
+// Full-rank (2-D) records: in0, in1, in2, sum_xi2, 0, sum_xi1, unit, steps; the
+// output gradient is coef[unit] (-sqrt(dN)) (sum_xi1, sum_xi2), each component
+// zero where that output is clamped (beta_k = clamp(o_k)).
 constexpr int kBwdWarps = 4;
 constexpr int kBwdRows = 16 * kBwdWarps;     // records per tile
 constexpr int kSX = 24;                      // row strides (bf16 elements), chosen
@@ -212,7 +215,7 @@ __device__ __forceinline__ void st_bf16x2(__nv_bfloat16 *p, float lo, float hi)
 __global__ void __launch_bounds__(kBwdWarps * 32)
 mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long long n_rec,
                const float *__restrict__ coef, float neg_sqrt_dN, float amax,
-               const float *__restrict__ dalpha_direct, float *__restrict__ grad)
+               const float *__restrict__ dalpha_direct, float *__restrict__ grad, int rank2)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
@@ -275,8 +278,19 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
             if (r < n_rec) {
                 const float *q = rec + 8 * r;
                 in0 = q[0]; in1 = q[1]; in2 = q[2]; tq = q[3];
-                if (dalpha_direct) da = dalpha_direct[r];
-                else da = coef[__float_as_uint(q[6])] * (neg_sqrt_dN * q[5]);
+                if (rank2) {
+                    // (tt, dal) = output gradients of o2 and o1 (direct: dalpha_direct[2r], [2r + 1])
+                    if (dalpha_direct) { da = dalpha_direct[2 * r]; tq = dalpha_direct[2 * r + 1]; }
+                    else {
+                        const float c = coef[__float_as_uint(q[6])] * neg_sqrt_dN;
+                        da = c * q[5];
+                        tq = c * q[3];
+                    }
+                } else if (dalpha_direct) {
+                    da = dalpha_direct[r];
+                } else {
+                    da = coef[__float_as_uint(q[6])] * (neg_sqrt_dN * q[5]);
+                }
             }
             __nv_bfloat16 *xr = S.x + tid * kSX;
             st_bf16x2(xr, in0, in1);
@@ -342,12 +356,20 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
         // d alpha / d o on rows r0, r1 (computed by the t == 0 lanes, shared in the quad)
         float do0a = 0.f, do1a = 0.f, do0b = 0.f, do1b = 0.f;
         if (t == 0) {
-            const float ta = S.tt[r0], tb = S.tt[r1];
-            const float ia = rsqrtf(fmaf(ta, ta, 1.0f)), ib = rsqrtf(fmaf(tb, tb, 1.0f));
-            const float rawa = (d3[0] + ta * d3[1]) * ia, rawb = (d3[2] + tb * d3[3]) * ib;
-            const float ca = fabsf(rawa) < amax ? S.dal[r0] * ia : 0.0f;
-            const float cb = fabsf(rawb) < amax ? S.dal[r1] * ib : 0.0f;
-            do0a = ca; do1a = ca * ta; do0b = cb; do1b = cb * tb;
+            if (rank2) {
+                // beta_k = clamp(o_k): each output passes its own gradient unless clamped
+                do0a = fabsf(d3[0]) < amax ? S.dal[r0] : 0.0f;
+                do1a = fabsf(d3[1]) < amax ? S.tt[r0] : 0.0f;
+                do0b = fabsf(d3[2]) < amax ? S.dal[r1] : 0.0f;
+                do1b = fabsf(d3[3]) < amax ? S.tt[r1] : 0.0f;
+            } else {
+                const float ta = S.tt[r0], tb = S.tt[r1];
+                const float ia = rsqrtf(fmaf(ta, ta, 1.0f)), ib = rsqrtf(fmaf(tb, tb, 1.0f));
+                const float rawa = (d3[0] + ta * d3[1]) * ia, rawb = (d3[2] + tb * d3[3]) * ib;
+                const float ca = fabsf(rawa) < amax ? S.dal[r0] * ia : 0.0f;
+                const float cb = fabsf(rawb) < amax ? S.dal[r1] * ib : 0.0f;
+                do0a = ca; do1a = ca * ta; do0b = cb; do1b = cb * tb;
+            }
             st_bf16x2(S.dout + r0 * kSX, do0a, do1a);
             st_bf16x2(S.dout + r1 * kSX, do0b, do1b);
         }
@@ -465,7 +487,8 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
 size_t mlp_bwd_smem() { return sizeof(BwdSmem); }
 
 cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_rec, const float *coef, float dN,
-                           float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s)
+                           float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s,
+                           int rank2)
 {
     const size_t smem = sizeof(BwdSmem);
     cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -474,7 +497,7 @@ cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_re
     const long long tiles = (n_rec + kBwdRows - 1) / kBwdRows;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count * 3);
     mlp_bwd_kernel<<<grid, kBwdWarps * 32, smem, s>>>(params, rec, n_rec, coef, -sqrtf(dN), amax,
-                                                      dalpha_direct, grad);
+                                                      dalpha_direct, grad, rank2);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,8 @@ _SIGNATURES = {
                                C.c_void_p, C.c_void_p, C.c_void_p]),
     "fpt_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                C.c_float, C.c_void_p, C.c_void_p]),
+    "fpt_mlp_grad2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                C.c_void_p, C.c_void_p]),
     "fpt_mlp_train_round": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_double,
                                       C.c_double, C.POINTER(fpt_adam), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(fpt_train_stats), C.c_void_p]),
@@ -490,6 +492,17 @@ def fpt_mlp_grad(ctx: Context, params, s, tan_t, dalpha, alpha_max: float, strea
     g = np.zeros(FPT_MLP_PARAMS, np.float32)
     _check(load().fpt_mlp_grad(ctx.handle, _ptr(params), _ptr(s), _ptr(t), _ptr(d), len(t), alpha_max,
                                _ptr(g), _stream(stream)), ctx.handle)
+    return g
+
+
+def fpt_mlp_grad2(ctx: Context, params, s, dbeta, alpha_max: float, stream=None):
+    """Gradient of sum(dbeta * beta(s)) for the 2-D bias beta = clamp(o)."""
+    p = np.ascontiguousarray(params, np.float32) if isinstance(params, np.ndarray) else params
+    sv = np.ascontiguousarray(s, np.float32)
+    d = np.ascontiguousarray(dbeta, np.float32)
+    g = np.zeros(FPT_MLP_PARAMS, np.float32)
+    _check(load().fpt_mlp_grad2(ctx.handle, _ptr(p), _ptr(sv), _ptr(d), len(sv), alpha_max, _ptr(g),
+                                _stream(stream)), ctx.handle)
     return g
 
 

@@ -183,3 +183,61 @@ def test_2d_call_rules(torch):
         fpt.fpt_noise_table2(ctx, 0, fpt.FPT_TABLE_USER2, 16, 1.0, -0.1, 0.2, (a, a * 0.1, a * 0.5))
         st, _ = gpu_run(ctx, [fpt.run_desc(0, 64, seed=1), fpt.run_desc(1, 64, seed=1, run_id=1)], [64, 64])
         assert st == fpt.FPT_OK
+
+
+def test_2d_mlp_gradient_matches_oracle(torch):
+    """Rank-2 mode of the backward kernel (beta = clamp(o), two output
+    gradients per record) against the FP64 backward: relative L2 error <= 2e-2,
+    cosine >= 0.999, and a clamped component passes no gradient."""
+    from oracle import mlp as OM
+    v, p = _rand_params(23, out_scale=1.0)
+    n = 5000
+    s = W.random_states(n, 24)
+    db = np.random.default_rng(25).normal(0, 1, (n, 2))
+    amax = 0.8                                   # some outputs clamp
+    m = W.BM.model
+    with fpt.fpt_init_model([m]) as ctx:
+        g = fpt.fpt_mlp_grad2(ctx, v, s, db, amax)
+    s32 = s.astype(np.float32).astype(np.float64)
+    o, _ = OM.forward(p, s32, round_bf16=True)
+    assert 0.05 < np.mean(np.abs(o) >= amax) < 0.95
+    gr = OM.beta_grad(p, s32, amax, db.astype(np.float32).astype(np.float64), round_bf16=True)
+    ref = fpt.canonical_params(gr).astype(np.float64)
+    got = g.astype(np.float64)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    cos = float(got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref)))
+    assert rel < 2e-2, rel
+    assert cos > 0.999, cos
+
+
+def test_2d_training_learns_the_exponential_tilt(torch):
+    """Training on 2-D noise: with S = diag(s, 0) the field is the drifted
+    walk and beta_2 moves nothing but adds weight variance, so the
+    zero-variance proposal for the target e^{lambda N} P is beta_1 = the Esscher
+    tilt alpha* = (mu - sqrt(mu^2 - 2 lambda s^2))/s and beta_2 = 0. Training from
+    a random second output must find both."""
+    mu, s_, lam = W.BM_MU, W.BM_S, 9.5
+    alpha_star = (mu - math.sqrt(mu * mu - 2 * lam * s_ * s_)) / s_
+    p0 = W.mlp_init(16, out_scale=0.0)
+    p0["b3"] = np.array([0.0, 0.8])
+    v0 = fpt.canonical_params(p0)
+    m = W.BM.model
+    z = np.zeros(16)
+    with fpt.fpt_init_model([m]) as ctx:
+        fpt.fpt_noise_table2(ctx, 0, fpt.FPT_TABLE_USER2, 16, 1.0, -0.1, 0.2, (np.full(16, s_), z, z))
+        prop = TR.new_proposal(ctx, v0, shift=(0.025, -0.01, 3.0), scale=(40.0, 100.0, 0.3),
+                               segment=64, alpha_max=4.0)
+        TR.train(ctx, prop, 0, rounds=120, n_traj=1 << 13, seed=18, lam=lam, N_cut=lambda r: 1e9, lr=1e-2)
+        h = prop.history
+        N = np.linspace(0.5, 4.5, 64)
+        x = 0.05 - (mu - alpha_star * s_) * N
+        st = np.stack([x, np.full(64, -mu), N], axis=1)
+        sn = (st - np.array(prop.shift)) * np.array(prop.scale)
+        _, o = fpt.fpt_mlp_eval(ctx, prop.blob, sn, np.zeros(64), 4.0)
+    o = o.reshape(64, 2)
+    print(f"2-D training: loss {h[0]['loss']:.3g} -> {h[-1]['loss']:.3g}, beta1 median "
+          f"{np.median(o[:, 0]):.4f} (alpha* {alpha_star:.4f}), |beta2| max {np.max(np.abs(o[:, 1])):.4f}")
+    assert h[-1]["loss"] < 0.1 * h[0]["loss"]
+    assert abs(np.median(o[:, 0]) / alpha_star - 1) < 0.1
+    assert np.all(np.abs(o[:, 0] / alpha_star - 1) < 0.3)
+    assert np.max(np.abs(o[:, 1])) < 0.15 * alpha_star

@@ -92,3 +92,41 @@ def test_log_variance_gradient_by_finite_differences():
             q[k][idx] -= 2 * h
             fd = (fp - L(q)) / (2 * h)
             assert abs(fd - g[k][idx]) <= 1e-5 * max(1e-3, abs(fd)) + 1e-9
+
+
+def test_log_variance_gradient_2d_by_finite_differences():
+    """2-D noise (Eq. 4.5 with B = S beta): dL/dtheta from the two noise sums
+    per segment equals the finite-difference derivative of
+    Var[ln w_theta + lambda N] over the same recorded full-rank paths, and the
+    recorded ln w equals the off-policy formula at the sampling parameters."""
+    m = W.BM.model
+    res = T.resolve(m)
+    tab = T.user_table2(np.full(16, 1e-3), np.full(16, 3e-4), np.full(16, 5e-4), -0.1, 0.2)
+    p = _params(out_scale=0.2)
+    shift, scale = [0.0, 0.0, 0.0], [20.0, 100.0, 0.2]
+    seg = 64
+    mlp = S.MLPBias(p, segment=seg, in_shift=shift, in_scale=scale, alpha_max=0.05, round_bf16=False)
+    trajs = [S.run2_segments(m, res, tab, mlp, seed=6, run_id=0, traj=j) for j in range(24)]
+    lam = 0.3
+    loss, g = M.logvar_loss_grad2(p, trajs, m.dN, lam, shift, scale, 0.05)
+    for tr in trajs:
+        assert M.logw_at2(p, tr, m.dN, shift, scale, 0.05, seg) == pytest.approx(tr["logw"], rel=1e-9, abs=1e-9)
+    assert any(np.any(np.abs(tr["beta"]) == 0.05) for tr in trajs)      # the clamp is exercised
+
+    def L(q):
+        Y = np.array([M.logw_at2(q, tr, m.dN, shift, scale, 0.05, seg) + lam * tr["nsteps"] * m.dN
+                      for tr in trajs])
+        return float(np.mean((Y - Y.mean()) ** 2))
+
+    assert L(p) == pytest.approx(loss, rel=1e-9)
+    rng = np.random.default_rng(5)
+    for k in M.KEYS:
+        for _ in range(3):
+            idx = tuple(rng.integers(0, d) for d in p[k].shape)
+            h = 1e-8      # small: no output may cross the clamp within the difference
+            q = {kk: v.copy() for kk, v in p.items()}
+            q[k][idx] += h
+            fp = L(q)
+            q[k][idx] -= 2 * h
+            fd = (fp - L(q)) / (2 * h)
+            assert abs(fd - g[k][idx]) <= 1e-5 * max(1e-3, abs(fd)) + 1e-7
