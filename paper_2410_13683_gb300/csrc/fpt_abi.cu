@@ -90,7 +90,7 @@ struct fpt_ctx {
     cudaStream_t last_stream = nullptr;
     cudaEvent_t run_done = nullptr;
 
-    fpt_launch launch{256, 0, 32, 1, 0.0};
+    fpt_launch launch{512, 0, 32, 1, 0.0};
     std::map<GraphKey, cudaGraphExec_t> graphs;
 
     // learned-proposal training scratch
@@ -729,7 +729,7 @@ fpt_status fpt_set_launch(fpt_ctx *ctx, const fpt_launch *l)
     if (l->check_steps < 0 || (l->check_steps % 4) || l->check_steps > 4096)
         return fail(ctx, FPT_E_INVALID, "check_steps must be a multiple of 4 in [4, 4096]");
     if (!(l->deadline_s >= 0) || !std::isfinite(l->deadline_s)) return fail(ctx, FPT_E_INVALID, "bad deadline");
-    ctx->launch.block = l->block ? l->block : 256;
+    ctx->launch.block = l->block ? l->block : 512;
     ctx->launch.blocks_per_sm = l->blocks_per_sm;
     ctx->launch.check_steps = l->check_steps ? l->check_steps : 32;
     ctx->launch.use_graph = l->use_graph;
@@ -889,8 +889,8 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
     const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
-    // the learned-proposal stepper is compiled for at most kMlpMaxBlock threads
-    const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
+    // the training-record stepper is compiled for at most kRecMaxBlock threads
+    const int block = var.rec ? std::min(ctx->launch.block, kRecMaxBlock) : ctx->launch.block;
     int occ = em_occupancy(var, block, smem_bytes);
     if (occ < 1) return fail(ctx, FPT_E_CUDA, "stepper does not fit on an SM with this shape");
     const int bps = ctx->launch.blocks_per_sm ? std::min(ctx->launch.blocks_per_sm, occ) : occ;
