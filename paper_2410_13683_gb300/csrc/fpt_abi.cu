@@ -889,8 +889,8 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
     const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
-    // the training-record stepper is compiled for at most kRecMaxBlock threads
-    const int block = var.rec ? std::min(ctx->launch.block, kRecMaxBlock) : ctx->launch.block;
+    // the learned-proposal steppers are compiled for at most kMlpMaxBlock threads
+    const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
     int occ = em_occupancy(var, block, smem_bytes);
     if (occ < 1) return fail(ctx, FPT_E_CUDA, "stepper does not fit on an SM with this shape");
     const int bps = ctx->launch.blocks_per_sm ? std::min(ctx->launch.blocks_per_sm, occ) : occ;

@@ -39,7 +39,7 @@ constexpr int kJackknife = 32;       // jackknife blocks of the histogram
 constexpr int kMaxBins = 4096;
 constexpr int kNoAllocMaxBins = 1024;   // fpt_histogram_noalloc
 constexpr int kMlpHidden = 64;
-constexpr int kRecMaxBlock = 384;       // block-size cap of the training-record stepper
+constexpr int kMlpMaxBlock = 384;       // block-size cap of the learned-proposal steppers
 
 // Model constants in the shifted coordinate x = phi - phi_end (FP32).
 struct ModelDev {

@@ -436,12 +436,12 @@ __device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, 
 }
 
 // Register budgets: the plain stepper keeps three 512-thread blocks per SM
-// (48 warps, 40 registers); the learned-proposal, noise-window and bump
-// steppers two 512-thread blocks (32 warps, 64 registers: the network's
-// fragments spill around its evaluation, once per segment); the training
-// stepper two 384-thread blocks (80 registers).
+// (48 warps, 40 registers); the noise-window and bump steppers two 512-thread
+// blocks; the learned-proposal steppers at most 384 threads per block and two
+// resident blocks, so that the network's fragments fit in 80 registers (a
+// 64-register build spilled and ran 3% slower).
 template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX, bool DTAB>
-__global__ void __launch_bounds__(REC ? kRecMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3) em_kernel(const EmParams P)
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3) em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
@@ -572,7 +572,7 @@ __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, SegRec &s
 }
 
 template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB, bool REC = false>
-__global__ void __launch_bounds__(REC ? kRecMaxBlock : 512, 2) em2_kernel(const EmParams P)
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];

@@ -194,7 +194,7 @@ def test_2d_mlp_gradient_matches_oracle(torch):
     n = 5000
     s = W.random_states(n, 24)
     db = np.random.default_rng(25).normal(0, 1, (n, 2))
-    amax = 0.8                                   # some outputs clamp
+    amax = 0.4                                   # about 14% of the outputs clamp
     m = W.BM.model
     with fpt.fpt_init_model([m]) as ctx:
         g = fpt.fpt_mlp_grad2(ctx, v, s, db, amax)
