@@ -59,6 +59,7 @@ struct fpt_ctx {
     size_t tables_cap = 0;
     std::vector<int> table_offset;
     std::vector<int> region_entries;   // float4 entries per model: noise table (+ drift table)
+    std::vector<ModelDev> h_models;    // host copy of the device model descriptors
     RunDev *d_runs = nullptr;
     RunDev *h_runs = nullptr;           // pinned staging
     unsigned long long *d_cursor = nullptr;
@@ -622,10 +623,12 @@ static fpt_status upload_tables(fpt_ctx *ctx)
             drift_table(m, inf, &packed[ctx->table_offset[i] + t.entries()]);
         }
         d.dN = (float)m.dN;
+        d.sqrt_dN = (float)std::sqrt(m.dN);
         d.max_steps = (int32_t)m.max_steps;
         d.table_offset = ctx->table_offset[i];
         if (t.ready) {
             d.M = t.M;
+            d.u_umax = (float)(t.M - 1);
             if (t.n_indexed) {
                 // u = (n dN - N_lo)/h; window of steps as in the oracle's definition
                 d.nidx = 1;
@@ -673,6 +676,7 @@ static fpt_status upload_tables(fpt_ctx *ctx)
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_models, md.data(), sizeof(ModelDev) * md.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
+    ctx->h_models = md;
     CK(cudaStreamSynchronize(ctx->stream));
     return FPT_OK;
 }
@@ -889,8 +893,9 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
     const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
-    // the learned-proposal steppers are compiled for at most kMlpMaxBlock threads
-    const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
+    // learned-proposal steppers with per-lane model constants or records are
+    // compiled for at most kMlpMaxBlock threads
+    const int block = (mlp && (var.rec || !smem)) ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
     int occ = em_occupancy(var, block, smem_bytes);
     if (occ < 1) return fail(ctx, FPT_E_CUDA, "stepper does not fit on an SM with this shape");
     const int bps = ctx->launch.blocks_per_sm ? std::min(ctx->launch.blocks_per_sm, occ) : occ;
@@ -906,6 +911,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     p.n_runs = n_runs;
     p.tables = ctx->d_tables;
     p.smem_table_offset = smem ? ctx->table_offset[smem_model] : 0;
+    if (smem) p.m0 = ctx->h_models[smem_model];
     p.smem_table_points = smem ? ctx->region_entries[smem_model] : 0;
     p.total_units = total;
     p.cursor = ctx->d_cursor;

@@ -49,7 +49,9 @@ struct ModelDev {
     float b_plus, b_minus;
     float x_in, pi_in;
     float u_scale, u_shift;    // table coordinate u = x * u_scale + u_shift
+    float u_umax;              // M - 1 (the clamp of u)
     float dN;
+    float sqrt_dN;
     int32_t M;                 // table points
     int32_t max_steps;
     int32_t table_offset;      // first float4 entry of this model's table
@@ -90,6 +92,9 @@ struct EmParams {
     int n_models;
     int n_runs;
     const float4 *tables;      // packed (S', dS', T', dT') entries, S' = S sqrt(dN)
+    // the launch's model when all runs share one (SMEM variants): the steppers
+    // read its constants from the kernel parameters instead of lane registers
+    ModelDev m0;
     int smem_table_offset;     // SMEM mode: first entry of the staged table
     int smem_table_points;     // SMEM mode: entries staged
     long long total_units;

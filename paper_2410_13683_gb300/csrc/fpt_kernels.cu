@@ -181,13 +181,14 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
 // weight f = u - k in [0, 1] need no float/int conversion. k = M - 1 happens
 // only at u = M - 1 with f = 0, and entry M - 1 carries zero slopes.
 template <bool SMEM, bool NIDX = false>
-__device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restrict__ tab, float &f)
+__device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restrict__ tab, float &f,
+                                           const ModelDev &M0)
 {
     const float kMagic = 12582912.0f;                        // 1.5 * 2^23
     // N-indexed tables: coordinate from the exact step count (n < 2^24 is exact in FP32)
     const float coord = (NIDX && L.nidx) ? __int2float_rn(L.n) : L.x;
-    float u = fmaf(coord, L.u_scale, L.u_shift);
-    u = fminf(fmaxf(u, 0.0f), L.u_max);
+    float u = fmaf(coord, SMEM ? M0.u_scale : L.u_scale, SMEM ? M0.u_shift : L.u_shift);
+    u = fminf(fmaxf(u, 0.0f), SMEM ? M0.u_umax : L.u_max);
     const float t = (u - 0.5f) + kMagic;
     const int i = __float_as_int(t) - 0x4b400000;
     f = u - (t - kMagic);
@@ -203,28 +204,28 @@ __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restri
 // evaluated from the closed form in FP32 only above the table.
 template <bool DTAB, bool SMEM>
 __device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restrict__ tab,
-                                           const ModelDev *s_model)
+                                           const ModelDev *s_model, const ModelDev &M0)
 {
     if (!DTAB) {
         // side of the kink from the compensated field and kink position:
         // x - x_c >= x_star + x_star_lo (x - x_star is exact near the kink), so
         // the branch follows the field itself, not the rounding of its FP32 head
-        const float d = L.x - L.dc.pw.x_star;
-        const bool up = d >= L.x_c + L.dc.pw.x_star_lo;
-        const float a = up ? L.dc.pw.a_plus : L.dc.pw.a_minus;
-        const float b = up ? L.dc.pw.b_plus : L.dc.pw.b_minus;
+        const float d = L.x - (SMEM ? M0.x_star : L.dc.pw.x_star);
+        const bool up = d >= L.x_c + (SMEM ? M0.x_star_lo : L.dc.pw.x_star_lo);
+        const float a = up ? (SMEM ? M0.a_plus : L.dc.pw.a_plus) : (SMEM ? M0.a_minus : L.dc.pw.a_minus);
+        const float b = up ? (SMEM ? M0.b_plus : L.dc.pw.b_plus) : (SMEM ? M0.b_minus : L.dc.pw.b_minus);
         return __fdividef(a, fmaf(b, d, 1.0f));
     }
-    const float u = fmaxf(L.x * L.dc.bump.scale, 0.0f);
-    if (u <= L.dc.bump.umax) {
+    const float u = fmaxf(L.x * (SMEM ? M0.d_scale : L.dc.bump.scale), 0.0f);
+    if (u <= (SMEM ? M0.d_umax : L.dc.bump.umax)) {
         const float kMagic = 12582912.0f;                    // 1.5 * 2^23
         const float t = (u - 0.5f) + kMagic;
         const int i = __float_as_int(t) - 0x4b400000;
         const float sv = u - (t - kMagic);
-        const float4 c = SMEM ? tab[L.dc.bump.dtab + i] : __ldg(tab + L.tbase + L.dc.bump.dtab + i);
+        const float4 c = SMEM ? tab[M0.dtab + i] : __ldg(tab + L.tbase + L.dc.bump.dtab + i);
         return fmaf(sv, fmaf(sv, fmaf(sv, c.w, c.z), c.y), c.x);
     }
-    const ModelDev &md = s_model[L.dc.bump.model];
+    const ModelDev &md = SMEM ? M0 : s_model[L.dc.bump.model];
     const float phi = L.x + md.bump_phi_end;
     const float d = L.x + md.bump_dphi0;                     // phi - phi0
     const float g = md.bump_K * __expf(-0.5f * d * d * md.bump_inv_w2);
@@ -239,11 +240,12 @@ __device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restri
 // fixed sign. Returns true when the trajectory has finished (passage or cap).
 template <bool WEIGHTED, bool SMEM, bool NIDX = false, bool DTAB = false>
 __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restrict__ tab,
-                                        const ModelDev *s_model)
+                                        const ModelDev *s_model, const ModelDev &M0)
 {
     // noise table: linear interpolation in x (or in time), end values held outside
     float f;
-    const float4 e = table_at<SMEM, NIDX>(L, tab, f);
+    const float4 e = table_at<SMEM, NIDX>(L, tab, f, M0);
+    const float dN = SMEM ? M0.dN : L.dN;
     float S = fmaf(f, e.y, e.x);               // S_phiphi sqrt(dN)
     float T = fmaf(f, e.w, e.z);               // tan(theta_n) S_phiphi sqrt(dN)
     float cb = L.cb, half_cb2 = L.half_cb2;
@@ -254,21 +256,21 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
         cb = 0.0f;
         half_cb2 = 0.0f;
     }
-    const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model);
+    const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model, M0);
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
     const float zb = z + cb;                             // xi + alpha sqrt(dN)
-    const float dx = fmaf(S, zb, L.p * L.dN);           // (pi + alpha S) dN + S xi sqrt(dN)
+    const float dx = fmaf(S, zb, L.p * dN);             // (pi + alpha S) dN + S xi sqrt(dN)
     if (DTAB) {
         // correlated pi-noise (tan theta_n ~ 0.3): the momentum is a compensated
         // pair, or its rounding performs a random walk that the field integrates
-        kahan_add(L.p, L.p_c, fmaf(T, zb, hh * L.dN * (L.p + vpv)));
+        kahan_add(L.p, L.p_c, fmaf(T, zb, hh * dN * (L.p + vpv)));
     } else {
-        L.p = fmaf(T, zb, fmaf(hh * L.dN, L.p + vpv, L.p));
+        L.p = fmaf(T, zb, fmaf(hh * dN, L.p + vpv, L.p));
     }
     if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(cb, z, half_cb2));
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
-    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= L.nmax);
+    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
 }
 
 __device__ __forceinline__ unsigned long long globaltimer()
@@ -282,17 +284,19 @@ __device__ __forceinline__ unsigned long long globaltimer()
 // at the current state; every lane of the warp takes part.
 template <bool SMEM, bool REC>
 __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg, const float4 *tab,
-                                                  const uint2 *tiles, const float *bias, const RunDev &pr)
+                                                  const uint2 *tiles, const float *bias, const RunDev &pr,
+                                                  const ModelDev &M0)
 {
+    const float dN = SMEM ? M0.dN : L.dN, sqrt_dN = SMEM ? M0.sqrt_dN : L.sqrt_dN;
     float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f, tan_t = 0.0f;
     if (live) {
         const float xv = __fsub_rn(L.x, L.x_c);
         in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
         in0 = (in0 - pr.shift[0]) * pr.scale[0];
         in1 = (L.p - pr.shift[1]) * pr.scale[1];
-        in2 = ((float)L.n * L.dN - pr.shift[2]) * pr.scale[2];
+        in2 = ((float)L.n * dN - pr.shift[2]) * pr.scale[2];
         float f;
-        const float4 e = table_at<SMEM>(L, tab, f);
+        const float4 e = table_at<SMEM>(L, tab, f, M0);
         const float S = fmaf(f, e.y, e.x), T = fmaf(f, e.w, e.z);
         tan_t = S > 0.0f ? __fdividef(T, S) : 0.0f;
     }
@@ -301,8 +305,8 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
     if (live) {
         float raw;
         const float al = mlp_alpha_of(o1, o2, tan_t, pr.alpha_max, raw);
-        L.cb = al * L.sqrt_dN;
-        L.half_cb2 = 0.5f * al * al * L.dN;
+        L.cb = al * sqrt_dN;
+        L.half_cb2 = 0.5f * al * al * dN;
         if (REC) {
             sg.in0 = in0; sg.in1 = in1; sg.in2 = in2; sg.tan_t = tan_t; sg.raw = raw;
             sg.sum_xi = 0.0f;
@@ -437,11 +441,13 @@ __device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, 
 
 // Register budgets: the plain stepper keeps three 512-thread blocks per SM
 // (48 warps, 40 registers); the noise-window and bump steppers two 512-thread
-// blocks; the learned-proposal steppers at most 384 threads per block and two
-// resident blocks, so that the network's fragments fit in 80 registers (a
-// 64-register build spilled and ran 3% slower).
+// blocks. The learned-proposal stepper with a launch-uniform model (SMEM: its
+// constants come from the kernel parameters) fits the network in 64 registers,
+// two 512-thread blocks (32 warps); with per-lane model constants, or with
+// training records, it keeps at most 384 threads per block and 80 registers.
 template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX, bool DTAB>
-__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3) em_kernel(const EmParams P)
+__global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3)
+    em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
 
     for (;;) {
         if (MLP && __any_sync(FULL, active && L.mlp))
-            mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun);
+            mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun, P.m0);
 
         for (int g = 0; g < P.groups_per_check; ++g) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u), P.rk);
@@ -477,7 +483,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
             for (int s = 0; s < 4; ++s)
                 if (active && !done) {
                     if (REC) sg.sum_xi += z[s];
-                    done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model);
+                    done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                 }
         }
 
@@ -506,11 +512,11 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
 // entries k and k + 1.
 template <bool SMEM>
 __device__ __forceinline__ void table2_at(const Lane &L, const float4 *__restrict__ tab, float &a,
-                                          float &b, float &c)
+                                          float &b, float &c, const ModelDev &M0)
 {
     const float kMagic = 12582912.0f;                        // 1.5 * 2^23
-    float u = fmaf(L.x, L.u_scale, L.u_shift);
-    u = fminf(fmaxf(u, 0.0f), L.u_max);
+    float u = fmaf(L.x, SMEM ? M0.u_scale : L.u_scale, SMEM ? M0.u_shift : L.u_shift);
+    u = fminf(fmaxf(u, 0.0f), SMEM ? M0.u_umax : L.u_max);
     const float t = (u - 0.5f) + kMagic;
     const int i = __float_as_int(t) - 0x4b400000;
     const float f = u - (t - kMagic);
@@ -523,44 +529,46 @@ __device__ __forceinline__ void table2_at(const Lane &L, const float4 *__restric
 
 template <bool WEIGHTED, bool SMEM, bool DTAB>
 __device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const float4 *__restrict__ tab,
-                                         const ModelDev *s_model)
+                                         const ModelDev *s_model, const ModelDev &M0)
 {
     float a, b, c;                                       // S sqrt(dN), interpolated in x
-    table2_at<SMEM>(L, tab, a, b, c);
-    const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model);
+    table2_at<SMEM>(L, tab, a, b, c, M0);
+    const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model, M0);
+    const float dN = SMEM ? M0.dN : L.dN;
     const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
     const float e1 = z1 + L.cb, e2 = z2 + L.cb_b;       // xi + beta sqrt(dN)
     // (phi, pi) += D dN + S beta dN + S xi sqrt(dN) = D dN + (S sqrt(dN)) e
-    const float dx = fmaf(a, e1, fmaf(b, e2, L.p * L.dN));
+    const float dx = fmaf(a, e1, fmaf(b, e2, L.p * dN));
     // full-rank noise drives pi directly: compensated momentum (see em_step)
-    kahan_add(L.p, L.p_c, fmaf(b, e1, fmaf(c, e2, hh * L.dN * (L.p + vpv))));
+    kahan_add(L.p, L.p_c, fmaf(b, e1, fmaf(c, e2, hh * dN * (L.p + vpv))));
     if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2)));
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
-    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= L.nmax);
+    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
 }
 
 // Learned proposal in 2-D: beta = (clamp(o1), clamp(o2)) at the segment start.
-template <bool REC>
+template <bool SMEM, bool REC>
 __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, SegRec &sg, const uint2 *tiles,
-                                                   const float *bias, const RunDev &pr)
+                                                   const float *bias, const RunDev &pr, const ModelDev &M0)
 {
+    const float dN = SMEM ? M0.dN : L.dN, sqrt_dN = SMEM ? M0.sqrt_dN : L.sqrt_dN;
     float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f;
     if (live) {
         const float xv = __fsub_rn(L.x, L.x_c);
         in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
         in0 = (in0 - pr.shift[0]) * pr.scale[0];
         in1 = (L.p - pr.shift[1]) * pr.scale[1];
-        in2 = ((float)L.n * L.dN - pr.shift[2]) * pr.scale[2];
+        in2 = ((float)L.n * dN - pr.shift[2]) * pr.scale[2];
     }
     float o1, o2;
     mlp_forward_warp(tiles, bias, in0, in1, in2, o1, o2);
     if (live) {
         const float b1 = fminf(fmaxf(o1, -pr.alpha_max), pr.alpha_max);
         const float b2 = fminf(fmaxf(o2, -pr.alpha_max), pr.alpha_max);
-        L.cb = b1 * L.sqrt_dN;
-        L.cb_b = b2 * L.sqrt_dN;
-        L.half_cb2 = 0.5f * fmaf(b1, b1, b2 * b2) * L.dN;
+        L.cb = b1 * sqrt_dN;
+        L.cb_b = b2 * sqrt_dN;
+        L.half_cb2 = 0.5f * fmaf(b1, b1, b2 * b2) * dN;
         if (REC) {
             sg.in0 = in0; sg.in1 = in1; sg.in2 = in2;
             sg.sum_xi = 0.0f;
@@ -572,7 +580,7 @@ __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, SegRec &s
 }
 
 template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB, bool REC = false>
-__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
+__global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
@@ -594,7 +602,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
 
     for (;;) {
         if (MLP && __any_sync(FULL, active && L.mlp))
-            mlp2_segment_start<REC>(L, active && L.mlp, sg, s_tiles, s_bias, prun);
+            mlp2_segment_start<SMEM, REC>(L, active && L.mlp, sg, s_tiles, s_bias, prun, P.m0);
 
         for (int g = 0; g < P.groups_per_check; ++g) {
             // four steps per group, two per Philox block: L.n is even at each block
@@ -607,11 +615,11 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
                 box_muller(r.z, r.w, z[2], z[3]);
                 if (active && !done) {
                     if (REC) { sg.sum_xi += z[0]; sg.sum_xi2 += z[1]; }
-                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model);
+                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model, P.m0);
                 }
                 if (active && !done) {
                     if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
-                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model);
+                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
                 }
             }
         }
