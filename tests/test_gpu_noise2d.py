@@ -195,12 +195,15 @@ def test_2d_mlp_gradient_matches_oracle(torch):
     s = W.random_states(n, 24)
     db = np.random.default_rng(25).normal(0, 1, (n, 2))
     amax = 0.4                                   # about 14% of the outputs clamp
-    m = W.BM.model
-    with fpt.fpt_init_model([m]) as ctx:
-        g = fpt.fpt_mlp_grad2(ctx, v, s, db, amax)
     s32 = s.astype(np.float32).astype(np.float64)
     o, _ = OM.forward(p, s32, round_bf16=True)
     assert 0.05 < np.mean(np.abs(o) >= amax) < 0.95
+    # outputs within 1e-2 of the clamp may fall on either side in bf16 arithmetic:
+    # they carry no gradient, so the comparison tests the mask, not the rounding
+    db[np.abs(np.abs(o) - amax) < 1e-2] = 0.0
+    m = W.BM.model
+    with fpt.fpt_init_model([m]) as ctx:
+        g = fpt.fpt_mlp_grad2(ctx, v, s, db, amax)
     gr = OM.beta_grad(p, s32, amax, db.astype(np.float32).astype(np.float64), round_bf16=True)
     ref = fpt.canonical_params(gr).astype(np.float64)
     got = g.astype(np.float64)
