@@ -367,6 +367,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / judge / direct legs")
     ap.add_argument("--no-2d", action="store_true", help="skip the full-rank (2-D) noise leg")
     ap.add_argument("--no-bump", action="store_true", help="skip the Gaussian-bump leg")
+    ap.add_argument("--pipeline", type=int, default=2, help="steps in flight (contexts / streams)")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -420,19 +421,56 @@ def main():
     else:
         launch = fpt.fpt_autotune(ctx, [desc(10_000)], fraction=0.25)
 
-    def one_step(step, ev=None, d=None):
+    # Pipeline: P contexts on P streams, each step's launch issued before the
+    # previous step's histogram is read back, so that the tail of one launch
+    # (its longest trajectories, with most lanes idle) overlaps the next one.
+    P = max(1, args.pipeline)
+    ctxs, streams = [ctx], [stream]
+    for _ in range(P - 1):
+        c = fpt.fpt_init_model([m], device=dev)
+        fpt.fpt_noise_table(c, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
+        fpt.fpt_set_launch(c, **{k: launch[k] for k in ("block", "blocks_per_sm", "check_steps", "use_graph")})
+        ctxs.append(c)
+        streams.append(torch.cuda.Stream())
+
+    def issue(k, step, ev=None, d=None):
+        c, st = ctxs[k % P], streams[k % P]
         if ev is not None:
-            ev[0].record(stream)
-        fpt.fpt_run(ctx, [d or desc(step)], stream=stream)
+            ev[0].record(st)
+        fpt.fpt_run(c, [d or desc(step)], stream=st)
         if ev is not None:
-            ev[1].record(stream)
-        h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+            ev[1].record(st)
+
+    def collect(k):
+        c, st = ctxs[k % P], streams[k % P]
+        h = fpt.fpt_histogram(c, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=st)
         sw, sw2 = shard.tail_sums(h)
         steps = (h["N_mean"] * h["n_passed"] + h["n_capped"] * m.max_steps * m.dN) / m.dN
         return sw, sw2, steps
 
-    for k in range(args.warmup):
-        one_step(100_000 + k)
+    def pipelined(K, step_of, ev=None, before=None, dfun=None):
+        """K steps, up to P in flight; returns the summed tail sums and steps."""
+        tot = [0.0, 0.0, 0.0]
+        for k in range(min(P - 1, K)):
+            if before:
+                before(k)
+            issue(k, step_of(k), ev[k] if ev else None, dfun(step_of(k)) if dfun else None)
+        for k in range(K):
+            j = k + P - 1
+            if j < K:
+                if before:
+                    before(j)
+                issue(j, step_of(j), ev[j] if ev else None, dfun(step_of(j)) if dfun else None)
+            r = collect(k)
+            for i in range(3):
+                tot[i] += r[i]
+        return tot
+
+    def one_step(step, ev=None, d=None):
+        issue(0, step, ev, d)
+        return collect(0)
+
+    pipelined(args.warmup, lambda k: 100_000 + k)
 
     clocks = Clocks(dev)
     if dist:
@@ -442,14 +480,15 @@ def main():
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     run_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-    sw_tot = sw2_tot = steps_tot = 0.0
-    t_start.record(stream)
-    for k in range(args.steps):
-        sw, sw2, st = one_step(k, run_ev[k])
-        sw_tot += sw
-        sw2_tot += sw2
-        steps_tot += st
-    t_end.record(stream)
+    t_start.record(streams[0])
+    for st in streams[1:]:
+        st.wait_event(t_start)
+    sw_tot, sw2_tot, steps_tot = pipelined(args.steps, lambda k: k, run_ev)
+    for st in streams[1:]:
+        e = torch.cuda.Event()
+        e.record(st)
+        streams[0].wait_event(e)
+    t_end.record(streams[0])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -473,13 +512,12 @@ def main():
         T_pin = torch.from_numpy(T_tab).pin_memory().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sw_e = sw2_e = 0.0
-        for k in range(args.steps):
-            fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, len(S_pin), 1.0, float("nan"), float("nan"),
-                                S_pin, T_pin)
-            sw, sw2, _ = one_step(500_000 + k)
-            sw_e += sw
-            sw2_e += sw2
+
+        def upload(k):
+            fpt.fpt_noise_table(ctxs[k % P], 0, fpt.FPT_TABLE_USER, len(S_pin), 1.0, float("nan"),
+                                float("nan"), S_pin, T_pin)
+
+        sw_e, sw2_e, _ = pipelined(args.steps, lambda k: 500_000 + k, before=upload)
         torch.cuda.synchronize()
         e2e_t = time.perf_counter() - t0
         sw_e, sw2_e = shard.merge_tail_sums(sw_e, sw2_e, dist, device="cuda")
@@ -489,19 +527,17 @@ def main():
         # the constant-bias judge (the method without the learned part)
         nj = 1 << 22
         jd = lambda k: fpt.run_desc(0, nj, seed=seed + 2, run_id=k, A=A_judge, traj_offset=rank * nj)
-        one_step(0, d=jd(900))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        swj = sw2j = 0.0
-        for k in range(3):
-            sw, sw2, _ = one_step(0, d=jd(k))
-            swj += sw
-            sw2j += sw2
-        e1.record(stream)
+        pipelined(1, lambda k: 900, dfun=jd)
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        swj, sw2j, _ = pipelined(4, lambda k: k, dfun=jd)     # as pipelined as the learned steps
+        torch.cuda.synchronize()
+        judge_t = time.perf_counter() - t0
         swj, sw2j = shard.merge_tail_sums(swj, sw2j, dist, device="cuda")
-        judge = shard.ess_of(swj, sw2j) / (e0.elapsed_time(e1) * 1e-3)
-        extras["fixed_bias"] = {"A": A_judge, "n_traj_per_step": nj, "ess_tail_per_s": judge}
+        judge = shard.ess_of(swj, sw2j) / judge_t
+        extras["fixed_bias"] = {"A": A_judge, "n_traj_per_step": nj, "ess_tail_per_s": judge,
+                                "timing": "host clock over 4 pipelined steps"}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # direct sampling on the same GPU: ESS_T = n * 1e-12 in expectation
         nd = 1 << 22
         fpt.fpt_run(ctx, [fpt.run_desc(0, nd, seed=seed + 1, run_id=0, traj_offset=rank * nd)], stream=stream)
@@ -534,8 +570,13 @@ def main():
         except Exception:
             traffic = None
     mean_run_ms = float(np.mean(run_ms))
-    rl = roofline(steps_tot / args.steps, mean_run_ms, sm_count, sm_max, traffic,
+    # P launches are in flight: each launch's own events overlap its neighbours,
+    # so the stepper's rate is taken over the timed region (launch interval =
+    # elapsed / steps; the histograms take ~0.3% of it)
+    interval_ms = 1e3 * elapsed / args.steps
+    rl = roofline(steps_tot / args.steps, interval_ms if P > 1 else mean_run_ms, sm_count, sm_max, traffic,
                   INSTR_PER_STEP_MLP if learned else INSTR_PER_STEP)
+    rl["launch_time"] = ("timed region / steps, %d launches in flight" % P) if P > 1 else "CUDA events per launch"
     if not learned:
         rl["kernel"] = "em_kernel<weighted, smem table>"
 
@@ -555,7 +596,7 @@ def main():
             "clocks": clk,
             "ess_tail_total": ess_total,
             "em_steps_per_step": steps_tot / args.steps,
-            "em_steps_per_s": steps_tot / (sum(run_ms) * 1e-3),
+            "em_steps_per_s": steps_tot / elapsed, "pipeline": P,
             "em_launch_ms": mean_run_ms}
     if train_info:
         line["train"] = train_info
@@ -573,8 +614,9 @@ def main():
                                 "sample": f"{args.cpu_traj} trajectories of the same workload with the "
                                           f"constant-bias proposal A={A_judge} ({nsteps} Euler-Maruyama "
                                           f"steps, {dt:.1f} s)"}
-    fpt.fpt_sync(ctx)
-    ctx.close()
+    for c in ctxs:
+        fpt.fpt_sync(c)
+        c.close()
     if rank == 0:
         print(json.dumps(line))
     if dist:
