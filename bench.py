@@ -390,7 +390,7 @@ def main():
     N_tail, A_judge = tail["N_12"], tail["A"]
     m = usr_model()
     learned = args.proposal == "learned"
-    n = args.n_traj or ((1 << 20) if learned else (1 << 22))
+    n = args.n_traj or (1 << 22)
     seed = 20260
     dev = torch.cuda.current_device()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
