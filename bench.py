@@ -66,6 +66,9 @@ INSTR_PER_STEP_2D = 87
 # Horner 3, load 1) instead of the closed form (6), and the compensated
 # momentum (+3).
 INSTR_PER_STEP_BUMP = 66
+# Noise-window stepper: the plain step with the table coordinate from the
+# step count (+1) and the window test with its four selects (+6).
+INSTR_PER_STEP_NIDX = 67
 # Training recipe of the learned proposal (log-variance loss towards
 # e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum).
 TRAIN = dict(rounds=300, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4)
@@ -290,6 +293,54 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     return out
 
 
+def window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm_max, autotune=True):
+    """The paper's production setting (Sec. 4.1): Bessel-matched noise indexed
+    by the time since the start along the background, on for the whole
+    background range [N_in, N_end] and off after it (classical completion):
+    direct-sampling throughput and issue roofline of the noise-window stepper,
+    and the tail ESS rate with the constant bias A."""
+    nd = 1 << 22
+    Nw = m.n_end - m.n_in
+    out = {"table": f"Bessel, sigma = 1, 4096 points over N in [0, {Nw:.4f}]", "n_traj_per_run": nd}
+    ctx = fpt.fpt_init_model([m], device=torch.cuda.current_device())
+    fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL_N, 4096, 1.0, 0.0, Nw)
+    if autotune:
+        fpt.fpt_autotune(ctx, [fpt.run_desc(0, nd, seed=seed + 11, run_id=99)], fraction=0.25)
+    d = lambda k, A_=0.0: fpt.run_desc(0, nd, seed=seed + 11, run_id=k, A=A_, traj_offset=rank * nd)
+    fpt.fpt_run(ctx, [d(100)], stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, steps = [], 0.0
+    for k in range(3):
+        e0.record(stream)
+        fpt.fpt_run(ctx, [d(k)], stream=stream)
+        e1.record(stream)
+        h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        steps += h["N_mean"] * h["n_passed"] / m.dN
+    t = sum(ms) * 1e-3
+    out["direct_traj_per_s"] = 3 * nd / t
+    out["em_steps_per_s"] = steps / t
+    rl = roofline(steps / 3, float(np.mean(ms)), sm_count, sm_max, None, INSTR_PER_STEP_NIDX)
+    rl["kernel"] = "em_kernel<direct, smem table, noise window>"
+    out["roofline"] = rl
+    fpt.fpt_run(ctx, [d(50, A)], stream=stream)
+    e0.record(stream)
+    sw = sw2 = 0.0
+    for k in range(3):
+        fpt.fpt_run(ctx, [d(60 + k, A)], stream=stream)
+        h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        a, b = shard.tail_sums(h)
+        sw += a
+        sw2 += b
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["fixed_bias"] = {"A": A, "ess_tail_per_s": shard.ess_of(sw, sw2) / (e0.elapsed_time(e1) * 1e-3)}
+    fpt.fpt_sync(ctx)
+    ctx.close()
+    return out
+
+
 def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max, autotune=True):
     """Gaussian-bump model (Sec. 4.3), 4096-point Bessel table at sigma = 1:
     direct-sampling throughput of the stepper with the tabulated drift, and the
@@ -367,6 +418,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / judge / direct legs")
     ap.add_argument("--no-2d", action="store_true", help="skip the full-rank (2-D) noise leg")
     ap.add_argument("--no-bump", action="store_true", help="skip the Gaussian-bump leg")
+    ap.add_argument("--no-window", action="store_true", help="skip the noise-window leg")
     ap.add_argument("--pipeline", type=int, default=2, help="steps in flight (contexts / streams)")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
@@ -555,6 +607,10 @@ def main():
             sm_max_2d = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
             extras["noise_2d"] = noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
                                               sm_count, sm_max_2d, autotune=not args.no_autotune)
+        if not args.no_window:
+            sm_max_w = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+            extras["noise_window"] = window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
+                                                sm_count, sm_max_w, autotune=not args.no_autotune)
         if not args.no_bump:
             sm_max_b = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
             extras["bump"] = bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max_b,
