@@ -100,7 +100,8 @@ struct RunSm {               // per-run constants staged in shared memory
 struct Lane {                // per-thread trajectory state and its constants
     float x, x_c;            // shifted field phi - phi_end as a Kahan pair: x - x_c
     float p, p_c;            // momentum; p_c compensates it (Kahan) in the variants with pi-noise
-    float lw_hi, lw_lo;
+    float lw_hi, lw_lo;      // ln w as a Kahan pair
+    float lw_grp;            // increments of the current 4-step group, added to the pair per group
     int n;
     int nmax;
     uint32_t traj, run_id;
@@ -172,6 +173,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.p_c = 0.0f;
     L.lw_hi = 0.0f;
     L.lw_lo = 0.0f;
+    L.lw_grp = 0.0f;
     L.n = 0;
 }
 
@@ -267,7 +269,7 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     } else {
         L.p = fmaf(T, zb, fmaf(hh * dN, L.p + vpv, L.p));
     }
-    if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(cb, z, half_cb2));
+    if (WEIGHTED) L.lw_grp -= fmaf(cb, z, half_cb2);
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
     return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
@@ -485,6 +487,11 @@ __global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, 
                     if (REC) sg.sum_xi += z[s];
                     done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                 }
+            // the group's weight increments (at most 4, so a plain FP32 sum) into the pair
+            if (WEIGHTED) {
+                kahan_add(L.lw_hi, L.lw_lo, L.lw_grp);
+                L.lw_grp = 0.0f;
+            }
         }
 
         if (REC) {
@@ -541,7 +548,7 @@ __device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const floa
     const float dx = fmaf(a, e1, fmaf(b, e2, L.p * dN));
     // full-rank noise drives pi directly: compensated momentum (see em_step)
     kahan_add(L.p, L.p_c, fmaf(b, e1, fmaf(c, e2, hh * dN * (L.p + vpv))));
-    if (WEIGHTED) kahan_add(L.lw_hi, L.lw_lo, -fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2)));
+    if (WEIGHTED) L.lw_grp -= fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2));
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
     return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
@@ -621,6 +628,10 @@ __global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, 
                     if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
                     done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
                 }
+            }
+            if (WEIGHTED) {
+                kahan_add(L.lw_hi, L.lw_lo, L.lw_grp);
+                L.lw_grp = 0.0f;
             }
         }
         // 2-D records: (inputs, sum xi_2), (0, sum xi_1, unit, steps)
