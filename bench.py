@@ -335,7 +335,9 @@ def window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm
         sw2 += b
     e1.record(stream)
     torch.cuda.synchronize()
-    out["fixed_bias"] = {"A": A, "ess_tail_per_s": shard.ess_of(sw, sw2) / (e0.elapsed_time(e1) * 1e-3)}
+    out["fixed_bias"] = {"A": A, "ess_tail_per_s": shard.ess_of(sw, sw2) / (e0.elapsed_time(e1) * 1e-3),
+                         "note": "the bias acts only inside the window; after it the classical completion "
+                                 "rarely reaches N_12"}
     fpt.fpt_sync(ctx)
     ctx.close()
     return out
