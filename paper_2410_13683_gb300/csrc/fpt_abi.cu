@@ -544,8 +544,10 @@ fpt_status fpt_model_get_info(const fpt_ctx *ctx, int32_t model, fpt_model_info 
 }
 
 // Re-pack every ready table into one float4 array and refresh the model
-// descriptors: entry j of a model = (S_j, S_{j+1} - S_j, T_j, T_{j+1} - T_j)
-// times sqrt(dN), in FP32.
+// descriptors. 1-D tables: entry j = ((S_j + S_{j+1})/2, S_{j+1} - S_j,
+// (T_j + T_{j+1})/2, T_{j+1} - T_j) times sqrt(dN), in FP32 (midpoint form,
+// see table_at); 2-D tables: the values (S_phiphi, S_phipi, S_pipi, 0) times
+// sqrt(dN) at the grid points, entry M repeating entry M - 1.
 // Cubic table of V'/V for the Gaussian bump (see drift_vpv in fpt_kernels.cu):
 // kDriftIntervals intervals over x = phi - phi_end in [0, X], X = 16 (phi_in -
 // phi_end), capped at the background start; Hermite coefficients from the FP64
@@ -597,16 +599,17 @@ static fpt_status upload_tables(fpt_ctx *ctx)
         std::memset(&d, 0, sizeof(d));
         d.x_star = (float)(m.phi_star - inf.phi_end);
         d.x_star_lo = (float)((m.phi_star - inf.phi_end) - (double)d.x_star);
+        // V'/V = 1 / (1/a + c (phi - phi_star)); a zero slope gives 1/a = inf and V'/V = 0
+        auto inv = [](double a) { return a == 0.0 ? INFINITY : (float)(1.0 / a); };
         if (m.kind == FPT_POT_EXP) {
-            d.a_plus = d.a_minus = (float)m.mu;
-            d.b_plus = d.b_minus = 0.0f;
+            d.inv_a_plus = d.inv_a_minus = inv(m.mu);
+            d.drift_c = 0.0f;
             d.x_star = 0.0f;
             d.x_star_lo = 0.0f;
         } else {
-            d.a_plus = (float)m.a_plus;
-            d.a_minus = (float)m.a_minus;
-            d.b_plus = (float)m.a_plus;
-            d.b_minus = (float)m.a_minus;
+            d.inv_a_plus = inv(m.a_plus);
+            d.inv_a_minus = inv(m.a_minus);
+            d.drift_c = 1.0f;
         }
         d.x_in = (float)(inf.phi_in - inf.phi_end);
         d.pi_in = (float)inf.pi_in;
@@ -642,6 +645,12 @@ static fpt_status upload_tables(fpt_ctx *ctx)
                 d.u_scale = (float)(1.0 / t.h);
                 d.u_shift = (float)((inf.phi_end - t.lo) / t.h);
             }
+            if (!t.rank2) {
+                // 1-D tables are read at the interval midpoints: u' = u - 1/2 in [-1/2, M - 3/2]
+                if (t.n_indexed) d.u_shift = (float)(-t.lo / t.h - 0.5);
+                else d.u_shift = (float)((inf.phi_end - t.lo) / t.h - 0.5);
+                d.u_umax = (float)(t.M - 1.5);
+            }
             const double sq = std::sqrt(m.dN);
             d.rank2 = t.rank2 ? 1 : 0;
             if (t.rank2) {
@@ -656,9 +665,9 @@ static fpt_status upload_tables(fpt_ctx *ctx)
             for (int j = 0; j < t.M; ++j) {
                 const int k = std::min(j + 1, t.M - 1);
                 float4 e;
-                e.x = (float)(t.S[j] * sq);
-                e.y = (float)((t.S[k] - t.S[j]) * sq);
-                e.z = (float)(t.T[j] * sq);
+                e.x = (float)(0.5 * (t.S[j] + t.S[k]) * sq);       // interval midpoint value
+                e.y = (float)((t.S[k] - t.S[j]) * sq);             // slope per grid interval
+                e.z = (float)(0.5 * (t.T[j] + t.T[k]) * sq);
                 e.w = (float)((t.T[k] - t.T[j]) * sq);
                 packed[ctx->table_offset[i] + j] = e;
             }

@@ -45,11 +45,11 @@ constexpr int kMlpMaxBlock = 384;       // block-size cap of the learned-proposa
 struct ModelDev {
     float x_star;              // phi_star - phi_end (FP32 head)
     float x_star_lo;           // phi_star - phi_end - x_star (FP32 tail)
-    float a_plus, a_minus;     // V'/V = a / (1 + b (x - x_star)), branch by sign
-    float b_plus, b_minus;
+    float inv_a_plus, inv_a_minus;   // V'/V = 1 / (1/a + c (x - x_star)), side by sign
+    float drift_c;             // 1: piecewise linear (relative slopes); 0: exponential (V'/V = mu)
     float x_in, pi_in;
-    float u_scale, u_shift;    // table coordinate u = x * u_scale + u_shift
-    float u_umax;              // M - 1 (the clamp of u)
+    float u_scale, u_shift;    // table coordinate u = x * u_scale + u_shift (1-D tables: minus 1/2)
+    float u_umax;              // upper clamp of u: M - 3/2 (1-D tables), M - 1 (2-D tables)
     float dN;
     float sqrt_dN;
     int32_t M;                 // table points

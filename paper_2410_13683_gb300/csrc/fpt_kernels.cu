@@ -46,6 +46,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20]
     return c;
 }
 
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 __device__ __forceinline__ float sqrt_approx(float v)
 {
     float r;
@@ -108,7 +115,7 @@ struct Lane {                // per-thread trajectory state and its constants
     float cb, half_cb2, dN, sqrt_dN;
     float cb_b;              // 2-D noise: beta_2 sqrt(dN) (cb = beta_1 sqrt(dN))
     union {                  // drift constants of the lane's potential
-        struct { float x_star, x_star_lo, a_plus, a_minus, b_plus, b_minus; } pw;   // piecewise-linear / exponential
+        struct { float x_star, x_star_lo, inv_a_plus, inv_a_minus, c; } pw;   // piecewise-linear / exponential
         struct { float scale, umax; int dtab, model; } bump;              // Gaussian bump: cubic V'/V table
     } dc;
     float u_scale, u_shift, u_max;
@@ -154,14 +161,13 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     } else {
         L.dc.pw.x_star = m.x_star;
         L.dc.pw.x_star_lo = m.x_star_lo;
-        L.dc.pw.a_plus = m.a_plus;
-        L.dc.pw.a_minus = m.a_minus;
-        L.dc.pw.b_plus = m.b_plus;
-        L.dc.pw.b_minus = m.b_minus;
+        L.dc.pw.inv_a_plus = m.inv_a_plus;
+        L.dc.pw.inv_a_minus = m.inv_a_minus;
+        L.dc.pw.c = m.drift_c;
     }
     L.u_scale = m.u_scale;
     L.u_shift = m.u_shift;
-    L.u_max = (float)(m.M - 1);
+    L.u_max = m.u_umax;
     L.tbase = m.table_offset;
     L.nidx = m.nidx != 0;
     L.win_lo = m.win_lo;
@@ -177,11 +183,13 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.n = 0;
 }
 
-// Table entry (S', dS', T', dT') and interpolation weight at the lane's field.
-// u = (phi - phi_lo)/h clamped to [0, M - 1]; the entry index k = round(u - 1/2)
-// comes from adding 1.5 2^23 (round to nearest in the mantissa), so index and
-// weight f = u - k in [0, 1] need no float/int conversion. k = M - 1 happens
-// only at u = M - 1 with f = 0, and entry M - 1 carries zero slopes.
+// Table entry and interpolation weight at the lane's field. The 1-D tables
+// hold, per interval k, the midpoint values (v_k + v_{k+1})/2 and the slopes
+// v_{k+1} - v_k of (S', T') (times sqrt(dN)); with u' = (phi - phi_lo)/h - 1/2
+// clamped to [-1/2, M - 3/2], k = round(u') comes from adding 1.5 2^23 (round
+// to nearest in the mantissa, no float/int conversion) and f' = u' - k lies in
+// [-1/2, 1/2]: v(u) = mid_k + f' slope_k. The last entry repeats v_{M-1} with
+// zero slope, so every reachable k (0 .. M-1) is a valid entry.
 template <bool SMEM, bool NIDX = false>
 __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restrict__ tab, float &f,
                                            const ModelDev &M0)
@@ -190,8 +198,8 @@ __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restri
     // N-indexed tables: coordinate from the exact step count (n < 2^24 is exact in FP32)
     const float coord = (NIDX && L.nidx) ? __int2float_rn(L.n) : L.x;
     float u = fmaf(coord, SMEM ? M0.u_scale : L.u_scale, SMEM ? M0.u_shift : L.u_shift);
-    u = fminf(fmaxf(u, 0.0f), SMEM ? M0.u_umax : L.u_max);
-    const float t = (u - 0.5f) + kMagic;
+    u = fminf(fmaxf(u, -0.5f), SMEM ? M0.u_umax : L.u_max);
+    const float t = u + kMagic;
     const int i = __float_as_int(t) - 0x4b400000;
     f = u - (t - kMagic);
     return SMEM ? tab[i] : __ldg(tab + L.tbase + i);
@@ -211,12 +219,14 @@ __device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restri
     if (!DTAB) {
         // side of the kink from the compensated field and kink position:
         // x - x_c >= x_star + x_star_lo (x - x_star is exact near the kink), so
-        // the branch follows the field itself, not the rounding of its FP32 head
+        // the branch follows the field itself, not the rounding of its FP32 head.
+        // V'/V = a / (1 + a d) = 1 / (1/a + d) on each side (c = 1; the
+        // exponential potential has c = 0 and V'/V = 1/(1/mu)).
         const float d = L.x - (SMEM ? M0.x_star : L.dc.pw.x_star);
         const bool up = d >= L.x_c + (SMEM ? M0.x_star_lo : L.dc.pw.x_star_lo);
-        const float a = up ? (SMEM ? M0.a_plus : L.dc.pw.a_plus) : (SMEM ? M0.a_minus : L.dc.pw.a_minus);
-        const float b = up ? (SMEM ? M0.b_plus : L.dc.pw.b_plus) : (SMEM ? M0.b_minus : L.dc.pw.b_minus);
-        return __fdividef(a, fmaf(b, d, 1.0f));
+        const float ia = up ? (SMEM ? M0.inv_a_plus : L.dc.pw.inv_a_plus)
+                            : (SMEM ? M0.inv_a_minus : L.dc.pw.inv_a_minus);
+        return rcp_approx(fmaf(SMEM ? M0.drift_c : L.dc.pw.c, d, ia));
     }
     const float u = fmaxf(L.x * (SMEM ? M0.d_scale : L.dc.bump.scale), 0.0f);
     if (u <= (SMEM ? M0.d_umax : L.dc.bump.umax)) {
