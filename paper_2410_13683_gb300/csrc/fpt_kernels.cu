@@ -82,7 +82,8 @@ __device__ __forceinline__ void box_muller(uint32_t r0, uint32_t r1, float &z0, 
     z1 = -rho * sn;
 }
 
-// Compensated (Kahan) accumulation hi + lo += v.
+// Compensated (Kahan) accumulation of v into the pair (hi, lo), whose value
+// is hi - lo: lo holds the amount by which hi overshoots the exact sum.
 __device__ __forceinline__ void kahan_add(float &hi, float &lo, float v)
 {
     const float y = __fsub_rn(v, lo);
@@ -381,7 +382,7 @@ __device__ __forceinline__ void refill_point(const EmParams &P, Lane &L, bool &a
     if (fin_me) {
         const bool passed = __fsub_rn(L.x, L.x_c) <= 0.0f;
         P.nsteps[L.unit] = L.n;
-        P.logw[L.unit] = (double)L.lw_hi + (double)L.lw_lo;
+        P.logw[L.unit] = (double)L.lw_hi - (double)L.lw_lo;     // the pair holds hi - lo
         P.status[L.unit] = passed ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
         if (!passed) atomicAdd(P.flags + 1, 1);
     }
@@ -497,8 +498,10 @@ __global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, 
                     if (REC) sg.sum_xi += z[s];
                     done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                 }
-            // the group's weight increments (at most 4, so a plain FP32 sum) into the pair
-            if (WEIGHTED) {
+            // the group's weight increments (at most 4, so a plain FP32 sum) into the
+            // pair; a lane that took no step in the group adds nothing (re-adding zero
+            // would re-round the pair, and how often depends on the launch shape)
+            if (WEIGHTED && L.lw_grp != 0.0f) {
                 kahan_add(L.lw_hi, L.lw_lo, L.lw_grp);
                 L.lw_grp = 0.0f;
             }
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, 
                     done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
                 }
             }
-            if (WEIGHTED) {
+            if (WEIGHTED && L.lw_grp != 0.0f) {
                 kahan_add(L.lw_hi, L.lw_lo, L.lw_grp);
                 L.lw_grp = 0.0f;
             }
