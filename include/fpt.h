@@ -304,7 +304,10 @@ typedef struct {
 /* Launch shape. Zero fields take the context defaults (or the autotuned
  * choice). */
 typedef struct {
-    int32_t block;          /* threads per block: 128, 192, 256, 384 or 512   */
+    int32_t block;          /* threads per block: 128, 192, 256, 384 or 512
+                               (default 512; learned-proposal launches over
+                               several models, and training rounds, use at
+                               most 384)                                      */
     int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid)        */
     int32_t check_steps;    /* steps between refill points (multiple of 4)     */
     int32_t use_graph;      /* 1: replay a captured CUDA graph per shape      */
