@@ -305,8 +305,7 @@ typedef struct {
  * choice). */
 typedef struct {
     int32_t block;          /* threads per block: 128, 192, 256, 384 or 512
-                               (default 512; learned-proposal launches over
-                               several models, and training rounds, use at
+                               (default 512; learned-proposal launches use at
                                most 384)                                      */
     int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid)        */
     int32_t check_steps;    /* steps between refill points (multiple of 4)     */

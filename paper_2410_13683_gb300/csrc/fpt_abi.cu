@@ -902,9 +902,8 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
     const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
                               (mlp ? (size_t)kMlpBlobBytes : 0);
-    // learned-proposal steppers with per-lane model constants or records are
-    // compiled for at most kMlpMaxBlock threads
-    const int block = (mlp && (var.rec || !smem)) ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
+    // the learned-proposal steppers are compiled for at most kMlpMaxBlock threads
+    const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
     int occ = em_occupancy(var, block, smem_bytes);
     if (occ < 1) return fail(ctx, FPT_E_CUDA, "stepper does not fit on an SM with this shape");
     const int bps = ctx->launch.blocks_per_sm ? std::min(ctx->launch.blocks_per_sm, occ) : occ;

@@ -454,12 +454,12 @@ __device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, 
 
 // Register budgets: the plain stepper keeps three 512-thread blocks per SM
 // (48 warps, 40 registers); the noise-window and bump steppers two 512-thread
-// blocks. The learned-proposal stepper with a launch-uniform model (SMEM: its
-// constants come from the kernel parameters) fits the network in 64 registers,
-// two 512-thread blocks (32 warps); with per-lane model constants, or with
-// training records, it keeps at most 384 threads per block and 80 registers.
+// blocks; the learned-proposal steppers at most 384 threads per block and two
+// blocks, 80 registers: the network's fragments fit without spilling (a
+// 64-register build ran 512-thread blocks but executed ~7% more instructions
+// per step, and the autotuner chose 384 threads for it anyway).
 template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX, bool DTAB>
-__global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3)
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3)
     em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
@@ -600,7 +600,7 @@ __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, SegRec &s
 }
 
 template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB, bool REC = false>
-__global__ void __launch_bounds__((MLP && (REC || !SMEM)) ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
+__global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
     __shared__ RunSm s_run[kMaxRuns];
