@@ -555,6 +555,7 @@ def main():
         elapsed = float(t.item())
     sw_tot, sw2_tot = shard.merge_tail_sums(sw_tot, sw2_tot, dist, device="cuda")
     ess_total = shard.ess_of(sw_tot, sw2_tot)
+    n_total = float(n) * args.steps * world
     value = ess_total / elapsed
 
     extras = {}
@@ -653,6 +654,11 @@ def main():
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "ess_tail_total": ess_total,
+            # the estimate itself, beside the oracle's (FP64, constant bias): the
+            # weights are exact, so a good proposal changes the error, not the value
+            "p_tail": {"value": sw_tot / n_total, "rel_se": math.sqrt(max(0.0, 1.0 / ess_total - 1.0 / n_total))
+                       if ess_total > 0 else None,
+                       "oracle": tail["ccdf_at_N_12"], "oracle_rel_se": tail["rel_se_at_N_12"]},
             "em_steps_per_step": steps_tot / args.steps,
             "em_steps_per_s": steps_tot / elapsed, "pipeline": P,
             "em_launch_ms": mean_run_ms}

@@ -41,6 +41,17 @@ struct TableHost {
 
 using GraphKey = std::tuple<int, int, int, int, size_t, int, int, int, long long, int>;
 
+// A captured fpt_run. The stepper takes its EmParams by value (Philox round
+// keys, launch-uniform model constants), and a graph keeps the values it was
+// captured with; before a replay whose parameters differ, the stepper node of
+// the executable graph is given the new ones.
+struct RunGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t stepper = nullptr;
+    EmParams params;
+};
+
 }  // namespace
 
 struct fpt_ctx {
@@ -92,7 +103,7 @@ struct fpt_ctx {
     cudaEvent_t run_done = nullptr;
 
     fpt_launch launch{512, 0, 32, 1, 0.0};
-    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, RunGraph> graphs;
 
     // learned-proposal training scratch
     float *d_records = nullptr;
@@ -133,7 +144,10 @@ static fpt_status cuda_fail(fpt_ctx *c, cudaError_t e, const char *what)
 
 static void clear_graphs(fpt_ctx *ctx)
 {
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : ctx->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
     ctx->graphs.clear();
 }
 
@@ -954,19 +968,47 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
                              (var.dtab ? 16 : 0) + 32 * p.mlp_run};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
-                cudaGraph_t g;
+                RunGraph rg;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t e = enqueue_run(ctx, p, var, grid, block, smem_bytes, n_runs, ctx->stream);
-                cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
-                if (e != cudaSuccess) { if (e2 == cudaSuccess) cudaGraphDestroy(g); return cuda_fail(ctx, e, "capture"); }
+                cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &rg.graph);
+                if (e != cudaSuccess) {
+                    if (e2 == cudaSuccess) cudaGraphDestroy(rg.graph);
+                    return cuda_fail(ctx, e, "capture");
+                }
                 if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-                cudaGraphExec_t ex;
-                e = cudaGraphInstantiate(&ex, g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-                it = ctx->graphs.emplace(key, ex).first;
+                // the one kernel node of the capture is the stepper
+                size_t n_nodes = 0;
+                e = cudaGraphGetNodes(rg.graph, nullptr, &n_nodes);
+                std::vector<cudaGraphNode_t> nodes(n_nodes);
+                if (e == cudaSuccess && n_nodes) e = cudaGraphGetNodes(rg.graph, nodes.data(), &n_nodes);
+                int n_kernels = 0;
+                for (size_t i = 0; e == cudaSuccess && i < n_nodes; ++i) {
+                    cudaGraphNodeType t;
+                    e = cudaGraphNodeGetType(nodes[i], &t);
+                    if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) {
+                        rg.stepper = nodes[i];
+                        ++n_kernels;
+                    }
+                }
+                if (e == cudaSuccess && n_kernels != 1) e = cudaErrorInvalidValue;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&rg.exec, rg.graph, 0);
+                if (e != cudaSuccess) {
+                    cudaGraphDestroy(rg.graph);
+                    return cuda_fail(ctx, e, "graph of the run");
+                }
+                it = ctx->graphs.emplace(key, rg).first;
+                std::memcpy(&it->second.params, &p, sizeof(EmParams));   // padding included
+            } else if (std::memcmp(&it->second.params, &p, sizeof(EmParams)) != 0) {
+                cudaKernelNodeParams kp;
+                CK(cudaGraphKernelNodeGetParams(it->second.stepper, &kp));
+                void *args[] = {&p};
+                kp.kernelParams = args;
+                kp.extra = nullptr;
+                CK(cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.stepper, &kp));
+                std::memcpy(&it->second.params, &p, sizeof(EmParams));
             }
-            CK(cudaGraphLaunch(it->second, s));
+            CK(cudaGraphLaunch(it->second.exec, s));
         } else {
             cudaError_t e = enqueue_run(ctx, p, var, grid, block, smem_bytes, n_runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "run launch");

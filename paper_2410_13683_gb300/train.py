@@ -27,6 +27,7 @@ class Proposal:
     alpha_max: float
     flags: int = 0
     history: List[dict] = field(default_factory=list)
+    selection: List[dict] = field(default_factory=list)
 
     def desc(self, model: int, n_traj: int, seed: int, run_id: int, traj_offset: int = 0):
         return fpt.run_desc(model, n_traj, seed=seed, run_id=run_id, traj_offset=traj_offset,
@@ -68,4 +69,45 @@ def train(ctx, prop: Proposal, model: int, rounds: int, n_traj: int, seed: int, 
         prop.history.append(st)
         if log:
             log(st)
+    return prop
+
+
+def tail_ess(ctx, prop: Proposal, model: int, n_traj: int, seed: int, run_id: int, N_tail: float,
+             max_steps: int, dN: float, stream=None) -> dict:
+    """One run of the proposal on n_traj fresh trajectories: the tail
+    effective sample size (sum_T w)^2 / sum_T w^2 over T = {N >= N_tail},
+    the tail probability estimate sum_T w / n, the EM steps the run took and
+    the tail ESS per step (the cost-aware figure of merit of a proposal)."""
+    run = prop.desc(model, n_traj, seed=seed, run_id=run_id)
+    fpt.fpt_run(ctx, [run], stream=stream)
+    h = fpt.fpt_histogram(ctx, 0, 0.0, 2.0 * N_tail, 256, N_tail=N_tail, stream=stream)
+    steps = h["N_mean"] * h["n_passed"] / dN + h["n_capped"] * float(max_steps)
+    ess = float(h["ess_tail"])
+    return {"ess_tail": ess, "p_tail": float(h["p_tail"]), "steps": steps,
+            "ess_per_step": ess / steps if steps > 0 else 0.0}
+
+
+def train_select(ctx, prop: Proposal, model: int, rounds: int, checkpoints, val_traj: int, val_seed: int,
+                 N_tail: float, max_steps: int, dN: float, **train_kw) -> Proposal:
+    """train() for `rounds` rounds with model selection on held-out runs: at
+    each round count in `checkpoints` (and at the end) the current proposal
+    is run on val_traj trajectories of Philox seed val_seed (run id = the
+    round count, independent of the training runs when val_seed differs from
+    the training seed), and the parameters with the most tail ESS per EM step
+    are kept and re-packed. The measurements go to prop.selection."""
+    import torch
+    stops = sorted({int(c) for c in checkpoints if 0 < int(c) < rounds} | {rounds})
+    best, best_params, done = -1.0, None, 0
+    for c in stops:
+        train(ctx, prop, model, rounds=c - done, first_round=done, **train_kw)
+        done = c
+        v = tail_ess(ctx, prop, model, val_traj, val_seed, c, N_tail, max_steps, dN)
+        v["round"] = c
+        prop.selection.append(v)
+        if v["ess_per_step"] > best:
+            best, best_params = v["ess_per_step"], prop.params.clone()
+    if best_params is not None:
+        prop.params.copy_(best_params)
+        fpt.fpt_mlp_pack(ctx, prop.params, prop.blob)
+        torch.cuda.synchronize()
     return prop

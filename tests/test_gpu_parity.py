@@ -192,6 +192,44 @@ def test_launch_shape_and_split_invariance(torch, usr512):
         assert np.array_equal(np.concatenate([parts[0]["logw"], parts[1]["logw"]]), ref["logw"])
 
 
+def test_graph_replay_takes_the_seed_and_the_current_table(torch):
+    """A replayed graph runs with the call's Philox key and the model's
+    current table constants: after a call of the same launch shape with
+    another seed, or after a new table of the same size on another field
+    range, the results are those of a fresh context without graphs."""
+    m = W.BM.model
+    n = 4096
+    S = W.BM_S * np.linspace(0.5, 1.5, 16)
+    cases = [(9, -0.1, 0.2), (10, -0.1, 0.2), (10, -0.2, 0.3), (9, -0.2, 0.3)]
+
+    def run(ctx, seed):
+        st, g = gpu_run(ctx, [fpt.run_desc(0, n, seed=seed, run_id=1, A=0.3)], [n])
+        assert st == fpt.FPT_OK
+        return g[0]
+
+    fresh = []
+    for seed, lo, hi in cases:
+        with fpt.fpt_init_model([m]) as c:
+            fpt.fpt_set_launch(c, use_graph=False)
+            fpt.fpt_noise_table(c, 0, fpt.FPT_TABLE_USER, 16, 1.0, lo, hi, S, np.zeros(16))
+            fresh.append(run(c, seed))
+    with fpt.fpt_init_model([m]) as ctx:
+        fpt.fpt_set_launch(ctx, use_graph=True)
+        table = None
+        for (seed, lo, hi), want in zip(cases, fresh):
+            if table != (lo, hi):
+                fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, 16, 1.0, lo, hi, S, np.zeros(16))
+                table = (lo, hi)
+            for rep in range(2):
+                g = run(ctx, seed)
+                assert np.array_equal(g["nsteps"], want["nsteps"]), (seed, lo, hi, rep)
+                assert np.array_equal(g["logw"], want["logw"]), (seed, lo, hi, rep)
+    # the four cases differ from one another
+    for i in range(len(cases)):
+        for j in range(i):
+            assert not np.array_equal(fresh[i]["nsteps"], fresh[j]["nsteps"])
+
+
 def test_device_outputs_and_streams(torch, usr512):
     m, res, tab = usr512
     n = 4096
