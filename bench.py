@@ -70,8 +70,12 @@ INSTR_PER_STEP_BUMP = 66
 # step count (+1) and the window test with its four selects (+6).
 INSTR_PER_STEP_NIDX = 67
 # Training recipe of the learned proposal (log-variance loss towards
-# e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum).
-TRAIN = dict(rounds=300, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4)
+# e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum), then
+# model selection: from round select_from on, every select_every rounds, the
+# proposal runs on val_traj held-out trajectories (Philox seed val_seed) and
+# the checkpoint with the most tail ESS per EM step is kept.
+TRAIN = dict(rounds=550, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4,
+             select_from=400, select_every=25, val_traj=1 << 22, val_seed=31337)
 SM_LANES = 128
 
 
@@ -217,8 +221,13 @@ def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
     lr = lambda r: TRAIN["lr0"] if r < 20 else max(TRAIN["lr_min"], TRAIN["lr0"] * 0.98 ** (r - 20))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    TR.train(ctx, prop, 0, rounds=TRAIN["rounds"], n_traj=TRAIN["n_traj"], seed=seed, lam=TRAIN["lam"],
-             N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 16)
+    m = usr_model()
+    TR.train_select(ctx, prop, 0, rounds=TRAIN["rounds"],
+                    checkpoints=range(TRAIN["select_from"], TRAIN["rounds"], TRAIN["select_every"]),
+                    val_traj=TRAIN["val_traj"], val_seed=TRAIN["val_seed"], N_tail=N_tail,
+                    max_steps=m.max_steps, dN=m.dN,
+                    n_traj=TRAIN["n_traj"], seed=seed, lam=TRAIN["lam"],
+                    N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 17)
     torch.cuda.synchronize()
     return prop, time.perf_counter() - t0
 
@@ -463,7 +472,11 @@ def main():
         train_info = {"rounds": len(h), "seconds": round(train_s, 2), "traj_per_round": TRAIN["n_traj"],
                       "lambda": TRAIN["lam"], "N_cut": N_tail, "final_loss": round(h[-1]["loss"], 3),
                       "first_loss": round(h[0]["loss"], 3), "segment": TRAIN["segment"],
-                      "alpha_max": TRAIN["alpha_max"], "inputs": "(ln x, pi, N)"}
+                      "alpha_max": TRAIN["alpha_max"], "inputs": "(ln x, pi, N)",
+                      "selection": {"val_traj": TRAIN["val_traj"], "criterion": "held-out tail ESS per EM step",
+                                    "kept_round": max(prop.selection, key=lambda v: v["ess_per_step"])["round"],
+                                    "checkpoints": [[v["round"], round(v["ess_tail"]), float("%.4g" % v["ess_per_step"])]
+                                                    for v in prop.selection]}}
 
     def desc(step, nn=n, offset=off):
         if learned:

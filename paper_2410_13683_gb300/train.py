@@ -58,11 +58,22 @@ def train(ctx, prop: Proposal, model: int, rounds: int, n_traj: int, seed: int, 
     if not hasattr(prop, "_adam"):
         prop._adam = (torch.zeros_like(prop.params), torch.zeros_like(prop.params))
     m, v = prop._adam
+    ch = chunk or n_traj
     for r in range(first_round, first_round + rounds):
         run = prop.desc(model, n_traj, seed=seed, run_id=r)
         lr_r = lr(r) if callable(lr) else lr
-        st = fpt.fpt_mlp_train_round(ctx, run, chunk or n_traj, lam, N_cut(r),
-                                     dict(lr=lr_r, step=r + 1, clip=clip), prop.params, m, v, prop.blob)
+        while True:
+            try:
+                st = fpt.fpt_mlp_train_round(ctx, run, ch, lam, N_cut(r),
+                                             dict(lr=lr_r, step=r + 1, clip=clip), prop.params, m, v, prop.blob)
+                break
+            except fpt.FptError as e:
+                # more segment records than the record buffer holds: the round
+                # left the parameters untouched, so it is redone in halves
+                if e.status != fpt.FPT_E_NOMEM or ch <= 1024:
+                    raise
+                ch = (ch + 1) // 2
+        st["chunk"] = ch
         st["round"] = r
         st["N_cut"] = N_cut(r)
         st["lr"] = lr_r
