@@ -72,10 +72,11 @@ INSTR_PER_STEP_NIDX = 67
 # Training recipe of the learned proposal (log-variance loss towards
 # e^{lambda min(N, N_cut)} P, N_cut raised to N_12 by a curriculum), then
 # model selection: from round select_from on, every select_every rounds, the
-# proposal runs on val_traj held-out trajectories (Philox seed val_seed) and
-# the checkpoint with the most tail ESS per EM step is kept.
+# proposal runs val_runs times on val_traj held-out trajectories (Philox seed
+# val_seed) and the checkpoint with the most pooled tail ESS per EM step is
+# kept.
 TRAIN = dict(rounds=550, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4,
-             select_from=400, select_every=25, val_traj=1 << 22, val_seed=31337)
+             select_from=450, select_every=25, val_traj=1 << 22, val_runs=4, val_seed=31337)
 SM_LANES = 128
 
 
@@ -224,7 +225,8 @@ def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
     m = usr_model()
     TR.train_select(ctx, prop, 0, rounds=TRAIN["rounds"],
                     checkpoints=range(TRAIN["select_from"], TRAIN["rounds"], TRAIN["select_every"]),
-                    val_traj=TRAIN["val_traj"], val_seed=TRAIN["val_seed"], N_tail=N_tail,
+                    val_traj=TRAIN["val_traj"], val_seed=TRAIN["val_seed"], val_runs=TRAIN["val_runs"],
+                    N_tail=N_tail,
                     max_steps=m.max_steps, dN=m.dN,
                     n_traj=TRAIN["n_traj"], seed=seed, lam=TRAIN["lam"],
                     N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 17)
@@ -300,6 +302,23 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     fpt.fpt_sync(ctx2)
     ctx2.close()
     return out
+
+
+def fixed_sweep(fpt, ctx, stream, seed, rank, N_tail, m, As, steps_per_s, n=1 << 20):
+    """Tail ESS per EM step of each constant amplitude A (one run of n
+    trajectories each), the implied ESS rate at steps_per_s (the whole job's
+    EM-step rate), and the best A."""
+    rows = {}
+    for k, A in enumerate(As):
+        fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=seed, run_id=k, A=A, traj_offset=rank * n)], stream=stream)
+        h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        steps = h["N_mean"] * h["n_passed"] / m.dN + h["n_capped"] * float(m.max_steps)
+        ess = float(h["ess_tail"])
+        rows[str(A)] = {"ess_tail": round(ess, 2), "em_steps": steps, "n_capped": int(h["n_capped"]),
+                        "ess_tail_per_s": ess / steps * steps_per_s if steps > 0 else 0.0}
+    best = max(rows, key=lambda a: rows[a]["ess_tail_per_s"])
+    return {"n_traj_per_A": n, "em_steps_per_s": steps_per_s, "per_A": rows, "best_A": float(best),
+            "best_ess_tail_per_s": rows[best]["ess_tail_per_s"]}
 
 
 def window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm_max, autotune=True):
@@ -473,7 +492,8 @@ def main():
                       "lambda": TRAIN["lam"], "N_cut": N_tail, "final_loss": round(h[-1]["loss"], 3),
                       "first_loss": round(h[0]["loss"], 3), "segment": TRAIN["segment"],
                       "alpha_max": TRAIN["alpha_max"], "inputs": "(ln x, pi, N)",
-                      "selection": {"val_traj": TRAIN["val_traj"], "criterion": "held-out tail ESS per EM step",
+                      "selection": {"val_traj": TRAIN["val_traj"] * TRAIN["val_runs"],
+                                    "criterion": "held-out tail ESS per EM step",
                                     "kept_round": max(prop.selection, key=lambda v: v["ess_per_step"])["round"],
                                     "checkpoints": [[v["round"], round(v["ess_tail"]), float("%.4g" % v["ess_per_step"])]
                                                     for v in prop.selection]}}
@@ -515,8 +535,9 @@ def main():
         steps = (h["N_mean"] * h["n_passed"] + h["n_capped"] * m.max_steps * m.dN) / m.dN
         return sw, sw2, steps
 
-    def pipelined(K, step_of, ev=None, before=None, dfun=None):
-        """K steps, up to P in flight; returns the summed tail sums and steps."""
+    def pipelined(K, step_of, ev=None, before=None, dfun=None, per_step=None):
+        """K steps, up to P in flight; returns the summed tail sums and steps
+        (and appends each step's tail ESS to per_step)."""
         tot = [0.0, 0.0, 0.0]
         for k in range(min(P - 1, K)):
             if before:
@@ -531,6 +552,8 @@ def main():
             r = collect(k)
             for i in range(3):
                 tot[i] += r[i]
+            if per_step is not None:
+                per_step.append(shard.ess_of(r[0], r[1]))
         return tot
 
     def one_step(step, ev=None, d=None):
@@ -550,7 +573,8 @@ def main():
     t_start.record(streams[0])
     for st in streams[1:]:
         st.wait_event(t_start)
-    sw_tot, sw2_tot, steps_tot = pipelined(args.steps, lambda k: k, run_ev)
+    ess_steps = []
+    sw_tot, sw2_tot, steps_tot = pipelined(args.steps, lambda k: k, run_ev, per_step=ess_steps)
     for st in streams[1:]:
         e = torch.cuda.Event()
         e.record(st)
@@ -585,7 +609,9 @@ def main():
             fpt.fpt_noise_table(ctxs[k % P], 0, fpt.FPT_TABLE_USER, len(S_pin), 1.0, float("nan"),
                                 float("nan"), S_pin, T_pin)
 
-        sw_e, sw2_e, _ = pipelined(args.steps, lambda k: 500_000 + k, before=upload)
+        # the timed steps' trajectories (same seed and run ids): the
+        # difference from `value` is the host path alone
+        sw_e, sw2_e, _ = pipelined(args.steps, lambda k: k, before=upload)
         torch.cuda.synchronize()
         e2e_t = time.perf_counter() - t0
         sw_e, sw2_e = shard.merge_tail_sums(sw_e, sw2_e, dist, device="cuda")
@@ -598,13 +624,18 @@ def main():
         pipelined(1, lambda k: 900, dfun=jd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        swj, sw2j, _ = pipelined(4, lambda k: k, dfun=jd)     # as pipelined as the learned steps
+        swj, sw2j, stj = pipelined(4, lambda k: k, dfun=jd)     # as pipelined as the learned steps
         torch.cuda.synchronize()
         judge_t = time.perf_counter() - t0
         swj, sw2j = shard.merge_tail_sums(swj, sw2j, dist, device="cuda")
         judge = shard.ess_of(swj, sw2j) / judge_t
         extras["fixed_bias"] = {"A": A_judge, "n_traj_per_step": nj, "ess_tail_per_s": judge,
                                 "timing": "host clock over 4 pipelined steps"}
+        # the other constant amplitudes: tail ESS per EM step on 2^20
+        # trajectories each, priced at the judge's pipelined EM-step rate
+        # (the constant-bias stepper's cost per step does not depend on A)
+        extras["fixed_bias_sweep"] = fixed_sweep(fpt, ctx, stream, seed + 3, rank, N_tail, m,
+                                                 W.USR_FIXED_BIAS.biases, stj / judge_t * world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # direct sampling on the same GPU: ESS_T = n * 1e-12 in expectation
         nd = 1 << 22
@@ -667,6 +698,9 @@ def main():
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "ess_tail_total": ess_total,
+            # each step's own tail ESS: with heavy-tailed weights a few paths
+            # decide sum w^2, and the spread shows it
+            "ess_tail_per_step": [round(e) for e in ess_steps],
             # the estimate itself, beside the oracle's (FP64, constant bias): the
             # weights are exact, so a good proposal changes the error, not the value
             "p_tail": {"value": sw_tot / n_total, "rel_se": math.sqrt(max(0.0, 1.0 / ess_total - 1.0 / n_total))
@@ -682,6 +716,8 @@ def main():
         line["gain_vs_direct"] = value / extras["direct"]["ess_tail_per_s"]
     if "fixed_bias" in extras and extras["fixed_bias"]["ess_tail_per_s"] > 0:
         line["gain_vs_fixed_bias"] = value / extras["fixed_bias"]["ess_tail_per_s"]
+    if "fixed_bias_sweep" in extras and extras["fixed_bias_sweep"]["best_ess_tail_per_s"] > 0:
+        line["gain_vs_best_fixed_bias"] = value / extras["fixed_bias_sweep"]["best_ess_tail_per_s"]
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import tables as OT
         res = OT.resolve(m)

@@ -83,36 +83,48 @@ def train(ctx, prop: Proposal, model: int, rounds: int, n_traj: int, seed: int, 
     return prop
 
 
-def tail_ess(ctx, prop: Proposal, model: int, n_traj: int, seed: int, run_id: int, N_tail: float,
+def tail_ess(ctx, prop: Proposal, model: int, n_traj: int, seed: int, run_ids, N_tail: float,
              max_steps: int, dN: float, stream=None) -> dict:
-    """One run of the proposal on n_traj fresh trajectories: the tail
-    effective sample size (sum_T w)^2 / sum_T w^2 over T = {N >= N_tail},
-    the tail probability estimate sum_T w / n, the EM steps the run took and
-    the tail ESS per step (the cost-aware figure of merit of a proposal)."""
-    run = prop.desc(model, n_traj, seed=seed, run_id=run_id)
-    fpt.fpt_run(ctx, [run], stream=stream)
-    h = fpt.fpt_histogram(ctx, 0, 0.0, 2.0 * N_tail, 256, N_tail=N_tail, stream=stream)
-    steps = h["N_mean"] * h["n_passed"] / dN + h["n_capped"] * float(max_steps)
-    ess = float(h["ess_tail"])
-    return {"ess_tail": ess, "p_tail": float(h["p_tail"]), "steps": steps,
+    """Runs of the proposal on n_traj fresh trajectories per run id (one id
+    or a list), pooled: the tail effective sample size (sum_T w)^2 / sum_T w^2
+    over T = {N >= N_tail}, the tail probability estimate sum_T w / n, the EM
+    steps taken and the tail ESS per step (the cost-aware figure of merit of a
+    proposal). Pooling several runs catches more of the rare large weights
+    that decide the ESS of a long production run."""
+    ids = [run_ids] if isinstance(run_ids, int) else list(run_ids)
+    sw = sw2 = steps = 0.0
+    for rid in ids:
+        run = prop.desc(model, n_traj, seed=seed, run_id=rid)
+        fpt.fpt_run(ctx, [run], stream=stream)
+        h = fpt.fpt_histogram(ctx, 0, 0.0, 2.0 * N_tail, 256, N_tail=N_tail, stream=stream)
+        steps += h["N_mean"] * h["n_passed"] / dN + h["n_capped"] * float(max_steps)
+        a = h["p_tail"] * h["n_total"]
+        sw += a
+        sw2 += a * a / h["ess_tail"] if h["ess_tail"] > 0 else 0.0
+    ess = sw * sw / sw2 if sw2 > 0 else 0.0
+    return {"ess_tail": ess, "p_tail": sw / (float(n_traj) * len(ids)), "steps": steps,
             "ess_per_step": ess / steps if steps > 0 else 0.0}
 
 
 def train_select(ctx, prop: Proposal, model: int, rounds: int, checkpoints, val_traj: int, val_seed: int,
-                 N_tail: float, max_steps: int, dN: float, **train_kw) -> Proposal:
+                 N_tail: float, max_steps: int, dN: float, val_runs: int = 1, **train_kw) -> Proposal:
     """train() for `rounds` rounds with model selection on held-out runs: at
-    each round count in `checkpoints` (and at the end) the current proposal
-    is run on val_traj trajectories of Philox seed val_seed (run id = the
-    round count, independent of the training runs when val_seed differs from
-    the training seed), and the parameters with the most tail ESS per EM step
-    are kept and re-packed. The measurements go to prop.selection."""
+    each round count c in `checkpoints` (and at the end) the current proposal
+    is run val_runs times on val_traj trajectories of Philox seed val_seed
+    (run ids 64 c + j, independent of the training runs when val_seed differs
+    from the training seed), and the parameters with the most pooled tail ESS
+    per EM step are kept and re-packed. The measurements go to
+    prop.selection."""
     import torch
+    if not 1 <= val_runs <= 64:
+        raise ValueError("val_runs must be in [1, 64]")
     stops = sorted({int(c) for c in checkpoints if 0 < int(c) < rounds} | {rounds})
     best, best_params, done = -1.0, None, 0
     for c in stops:
         train(ctx, prop, model, rounds=c - done, first_round=done, **train_kw)
         done = c
-        v = tail_ess(ctx, prop, model, val_traj, val_seed, c, N_tail, max_steps, dN)
+        v = tail_ess(ctx, prop, model, val_traj, val_seed, [64 * c + j for j in range(val_runs)], N_tail,
+                     max_steps, dN)
         v["round"] = c
         prop.selection.append(v)
         if v["ess_per_step"] > best:

@@ -185,10 +185,11 @@ def test_training_learns_the_exponential_tilt(torch):
 
 
 def test_train_select_keeps_the_best_checkpoint(torch):
-    """Model selection on held-out runs: one measurement per checkpoint, the
-    kept parameters are the ones with the most tail ESS per EM step, and
-    running them again on the same held-out trajectories reproduces that
-    figure (the blob was re-packed from the kept parameters)."""
+    """Model selection on held-out runs: one pooled measurement (two runs)
+    per checkpoint, the kept parameters are the ones with the most tail ESS
+    per EM step, and running them again on the same held-out trajectories
+    reproduces that figure (the blob was re-packed from the kept
+    parameters)."""
     m = W.BM.model
     N_tail = 5.6
     v0 = fpt.canonical_params(W.mlp_init(16, out_scale=0.0))
@@ -196,12 +197,20 @@ def test_train_select_keeps_the_best_checkpoint(torch):
         prop = TR.new_proposal(ctx, v0, shift=(0.025, -0.01, 3.0), scale=(40.0, 100.0, 0.3),
                                segment=64, alpha_max=4.0)
         TR.train_select(ctx, prop, 0, rounds=60, checkpoints=[20, 40], val_traj=1 << 14, val_seed=91,
-                        N_tail=N_tail, max_steps=m.max_steps, dN=m.dN,
+                        N_tail=N_tail, max_steps=m.max_steps, dN=m.dN, val_runs=2,
                         n_traj=1 << 13, seed=17, lam=9.5, N_cut=lambda r: 1e9, lr=1e-2)
         sel = prop.selection
         assert [v["round"] for v in sel] == [20, 40, 60]
         assert all(v["ess_tail"] > 0 and v["p_tail"] > 0 for v in sel)
         best = max(sel, key=lambda v: v["ess_per_step"])
-        again = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, best["round"], N_tail, m.max_steps, m.dN)
+        c = best["round"]
+        again = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, [64 * c, 64 * c + 1], N_tail, m.max_steps, m.dN)
+        # the pooled figure is the ESS of the two runs' tail sums together
+        one = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, 64 * c, N_tail, m.max_steps, m.dN)
+        two = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, 64 * c + 1, N_tail, m.max_steps, m.dN)
+    sw = one["p_tail"] * (1 << 14) + two["p_tail"] * (1 << 14)
+    sw2 = (one["p_tail"] * (1 << 14)) ** 2 / one["ess_tail"] + (two["p_tail"] * (1 << 14)) ** 2 / two["ess_tail"]
+    assert again["ess_tail"] == pytest.approx(sw * sw / sw2, rel=1e-9)
+    assert again["steps"] == pytest.approx(one["steps"] + two["steps"], rel=1e-12)
     assert again["ess_per_step"] == pytest.approx(best["ess_per_step"], rel=1e-9)
     assert again["steps"] == pytest.approx(best["steps"], rel=1e-12)
