@@ -78,6 +78,9 @@ INSTR_PER_STEP_NIDX = 67
 TRAIN = dict(rounds=550, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4,
              select_from=450, select_every=25, val_traj=1 << 22, val_runs=4, val_seed=31337)
 SM_LANES = 128
+# Constant amplitudes compared with the learned proposal. Larger ones send the
+# paths past the step cap (2^19 steps): at A = 1 85% of them, at A >= 3 all.
+FIXED_SWEEP = (0.25, 0.375, 0.5, 0.625, 0.75, 1.0)
 
 
 def _env_int(k, d):
@@ -266,7 +269,7 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
         h = fpt.fpt_histogram(ctx2, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-        steps += h["N_mean"] * h["n_passed"] / m.dN
+        steps += passed_steps(h, m.dN)
     t = sum(ms) * 1e-3
     out["direct_traj_per_s"] = 3 * nd / t
     out["em_steps_per_s"] = steps / t
@@ -304,7 +307,13 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     return out
 
 
-def fixed_sweep(fpt, ctx, stream, seed, rank, N_tail, m, As, steps_per_s, n=1 << 20):
+def passed_steps(h, dN):
+    """EM steps of the passed trajectories of a histogram result (N_mean is
+    NaN when none passed)."""
+    return h["N_mean"] * h["n_passed"] / dN if h["n_passed"] > 0 else 0.0
+
+
+def fixed_sweep(fpt, ctx, stream, seed, rank, N_tail, m, As, steps_per_s, n=1 << 21):
     """Tail ESS per EM step of each constant amplitude A (one run of n
     trajectories each), the implied ESS rate at steps_per_s (the whole job's
     EM-step rate), and the best A."""
@@ -312,7 +321,7 @@ def fixed_sweep(fpt, ctx, stream, seed, rank, N_tail, m, As, steps_per_s, n=1 <<
     for k, A in enumerate(As):
         fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=seed, run_id=k, A=A, traj_offset=rank * n)], stream=stream)
         h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
-        steps = h["N_mean"] * h["n_passed"] / m.dN + h["n_capped"] * float(m.max_steps)
+        steps = passed_steps(h, m.dN) + h["n_capped"] * float(m.max_steps)
         ess = float(h["ess_tail"])
         rows[str(A)] = {"ess_tail": round(ess, 2), "em_steps": steps, "n_capped": int(h["n_capped"]),
                         "ess_tail_per_s": ess / steps * steps_per_s if steps > 0 else 0.0}
@@ -345,7 +354,7 @@ def window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, sm
         h = fpt.fpt_histogram(ctx, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-        steps += h["N_mean"] * h["n_passed"] / m.dN
+        steps += passed_steps(h, m.dN)
     t = sum(ms) * 1e-3
     out["direct_traj_per_s"] = 3 * nd / t
     out["em_steps_per_s"] = steps / t
@@ -400,7 +409,7 @@ def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max, autotune=T
         h = fpt.fpt_histogram(ctx, 0, 3.0, 5.0, 200, stream=stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-        steps += h["N_mean"] * h["n_passed"] / m.dN
+        steps += passed_steps(h, m.dN)
     t = sum(ms) * 1e-3
     out["direct_traj_per_s"] = 3 * nd / t
     out["em_steps_per_s"] = steps / t
@@ -532,7 +541,7 @@ def main():
         c, st = ctxs[k % P], streams[k % P]
         h = fpt.fpt_histogram(c, 0, 0.0, 400.0, 512, N_tail=N_tail, stream=st)
         sw, sw2 = shard.tail_sums(h)
-        steps = (h["N_mean"] * h["n_passed"] + h["n_capped"] * m.max_steps * m.dN) / m.dN
+        steps = passed_steps(h, m.dN) + h["n_capped"] * float(m.max_steps)
         return sw, sw2, steps
 
     def pipelined(K, step_of, ev=None, before=None, dfun=None, per_step=None):
@@ -631,11 +640,11 @@ def main():
         judge = shard.ess_of(swj, sw2j) / judge_t
         extras["fixed_bias"] = {"A": A_judge, "n_traj_per_step": nj, "ess_tail_per_s": judge,
                                 "timing": "host clock over 4 pipelined steps"}
-        # the other constant amplitudes: tail ESS per EM step on 2^20
-        # trajectories each, priced at the judge's pipelined EM-step rate
-        # (the constant-bias stepper's cost per step does not depend on A)
+        # other constant amplitudes around the judge's: tail ESS per EM step
+        # on 2^21 trajectories each, priced at the judge's pipelined EM-step
+        # rate (the constant-bias stepper's cost per step does not depend on A)
         extras["fixed_bias_sweep"] = fixed_sweep(fpt, ctx, stream, seed + 3, rank, N_tail, m,
-                                                 W.USR_FIXED_BIAS.biases, stj / judge_t * world)
+                                                 FIXED_SWEEP, stj / judge_t * world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # direct sampling on the same GPU: ESS_T = n * 1e-12 in expectation
         nd = 1 << 22

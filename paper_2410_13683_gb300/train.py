@@ -97,7 +97,9 @@ def tail_ess(ctx, prop: Proposal, model: int, n_traj: int, seed: int, run_ids, N
         run = prop.desc(model, n_traj, seed=seed, run_id=rid)
         fpt.fpt_run(ctx, [run], stream=stream)
         h = fpt.fpt_histogram(ctx, 0, 0.0, 2.0 * N_tail, 256, N_tail=N_tail, stream=stream)
-        steps += h["N_mean"] * h["n_passed"] / dN + h["n_capped"] * float(max_steps)
+        if h["n_passed"] > 0:        # N_mean is NaN when no trajectory passed
+            steps += h["N_mean"] * h["n_passed"] / dN
+        steps += h["n_capped"] * float(max_steps)
         a = h["p_tail"] * h["n_total"]
         sw += a
         sw2 += a * a / h["ess_tail"] if h["ess_tail"] > 0 else 0.0
