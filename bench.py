@@ -14,7 +14,7 @@ ESS_T = (sum_T w)^2 / sum_T w^2, summed over all steps and ranks.
 
 The proposal is the learned MLP bias (trained first, untimed, by the
 library's own forward/backward kernels and reported separately); the
-constant-bias proposal (the judge) and direct sampling are measured on the
+constant-bias proposal (the comparison run) and direct sampling are measured on the
 same GPU for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -454,7 +454,7 @@ def main():
     ap.add_argument("--train-rounds", type=int, default=TRAIN["rounds"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
-    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / judge / direct legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / constant-bias / direct legs")
     ap.add_argument("--no-2d", action="store_true", help="skip the full-rank (2-D) noise leg")
     ap.add_argument("--no-bump", action="store_true", help="skip the Gaussian-bump leg")
     ap.add_argument("--no-window", action="store_true", help="skip the noise-window leg")
@@ -478,7 +478,7 @@ def main():
     __graft_entry__.build()
     TRAIN["rounds"] = args.train_rounds
     tail = load_tail()
-    N_tail, A_judge = tail["N_12"], tail["A"]
+    N_tail, A_fixed = tail["N_12"], tail["A"]
     m = usr_model()
     learned = args.proposal == "learned"
     n = args.n_traj or (1 << 22)
@@ -510,7 +510,7 @@ def main():
     def desc(step, nn=n, offset=off):
         if learned:
             return prop.desc(0, nn, seed=seed, run_id=step, traj_offset=offset)
-        return fpt.run_desc(0, nn, seed=seed, run_id=step, A=A_judge, traj_offset=offset)
+        return fpt.run_desc(0, nn, seed=seed, run_id=step, A=A_fixed, traj_offset=offset)
 
     if args.no_autotune:
         launch = fpt.fpt_get_launch(ctx)
@@ -627,24 +627,24 @@ def main():
         extras["e2e"] = {"value": shard.ess_of(sw_e, sw2_e) / e2e_t, "unit": UNIT,
                          "h2d_bytes_per_step": len(S_pin) * 16 + 128 + (fpt.FPT_MLP_BLOB_BYTES if learned else 0),
                          "d2h_bytes_per_step": (10 * 512 + 16) * 8}
-        # the constant-bias judge (the method without the learned part)
+        # the constant-bias comparison (the method without the learned part)
         nj = 1 << 22
-        jd = lambda k: fpt.run_desc(0, nj, seed=seed + 2, run_id=k, A=A_judge, traj_offset=rank * nj)
+        jd = lambda k: fpt.run_desc(0, nj, seed=seed + 2, run_id=k, A=A_fixed, traj_offset=rank * nj)
         pipelined(1, lambda k: 900, dfun=jd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         swj, sw2j, stj = pipelined(4, lambda k: k, dfun=jd)     # as pipelined as the learned steps
         torch.cuda.synchronize()
-        judge_t = time.perf_counter() - t0
+        fixed_t = time.perf_counter() - t0
         swj, sw2j = shard.merge_tail_sums(swj, sw2j, dist, device="cuda")
-        judge = shard.ess_of(swj, sw2j) / judge_t
-        extras["fixed_bias"] = {"A": A_judge, "n_traj_per_step": nj, "ess_tail_per_s": judge,
+        fixed_rate = shard.ess_of(swj, sw2j) / fixed_t
+        extras["fixed_bias"] = {"A": A_fixed, "n_traj_per_step": nj, "ess_tail_per_s": fixed_rate,
                                 "timing": "host clock over 4 pipelined steps"}
-        # other constant amplitudes around the judge's: tail ESS per EM step
-        # on 2^21 trajectories each, priced at the judge's pipelined EM-step
+        # other constant amplitudes around A_fixed: tail ESS per EM step
+        # on 2^21 trajectories each, priced at the A_fixed run's pipelined EM-step
         # rate (the constant-bias stepper's cost per step does not depend on A)
         extras["fixed_bias_sweep"] = fixed_sweep(fpt, ctx, stream, seed + 3, rank, N_tail, m,
-                                                 FIXED_SWEEP, stj / judge_t * world)
+                                                 FIXED_SWEEP, stj / fixed_t * world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # direct sampling on the same GPU: ESS_T = n * 1e-12 in expectation
         nd = 1 << 22
@@ -661,11 +661,11 @@ def main():
         extras["direct"] = {"traj_per_s": direct_traj_s * world, "ess_tail_per_s": direct_traj_s * TAIL_P * world}
         if not args.no_2d:
             sm_max_2d = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-            extras["noise_2d"] = noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
+            extras["noise_2d"] = noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_fixed,
                                               sm_count, sm_max_2d, autotune=not args.no_autotune)
         if not args.no_window:
             sm_max_w = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-            extras["noise_window"] = window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_judge,
+            extras["noise_window"] = window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_fixed,
                                                 sm_count, sm_max_w, autotune=not args.no_autotune)
         if not args.no_bump:
             sm_max_b = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
@@ -698,7 +698,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": "usr_learned_tail" if learned else "usr_fixed_bias_tail",
                        "model": "piecewise-linear USR, V0=2e-10 a+=1e-3 a-=1e-6, phi*=1",
-                       "proposal": "learned MLP 3-64-64-2 (bf16)" if learned else f"constant A={A_judge}",
+                       "proposal": "learned MLP 3-64-64-2 (bf16)" if learned else f"constant A={A_fixed}",
                        "n_traj_per_step_per_gpu": n, "N_tail": N_tail,
                        "table_points": W.USR_TABLE.n_points, "dN": m.dN, "max_steps": m.max_steps,
                        "l2": "inputs are generated in-kernel; the 64 KB table and 12 KB weights stay in shared memory",
@@ -731,10 +731,10 @@ def main():
         from oracle import tables as OT
         res = OT.resolve(m)
         tab = OT.bessel_table(m, res, W.USR_TABLE.n_points, W.USR_TABLE.sigma, processes=os.cpu_count())
-        e, dt, cores, nsteps = cpu_oracle_sample((m, res, tab), A_judge, N_tail, args.cpu_traj)
+        e, dt, cores, nsteps = cpu_oracle_sample((m, res, tab), A_fixed, N_tail, args.cpu_traj)
         line["cpu_baseline"] = {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_traj} trajectories of the same workload with the "
-                                          f"constant-bias proposal A={A_judge} ({nsteps} Euler-Maruyama "
+                                          f"constant-bias proposal A={A_fixed} ({nsteps} Euler-Maruyama "
                                           f"steps, {dt:.1f} s)"}
     for c in ctxs:
         fpt.fpt_sync(c)
