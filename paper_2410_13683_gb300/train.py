@@ -134,5 +134,6 @@ def train_select(ctx, prop: Proposal, model: int, rounds: int, checkpoints, val_
     if best_params is not None:
         prop.params.copy_(best_params)
         fpt.fpt_mlp_pack(ctx, prop.params, prop.blob)
-        torch.cuda.synchronize()
+        if prop.params.is_cuda:
+            torch.cuda.synchronize()
     return prop
