@@ -309,7 +309,9 @@ typedef struct {
                                most 384)                                      */
     int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid)        */
     int32_t check_steps;    /* steps between refill points (multiple of 4)     */
-    int32_t use_graph;      /* 1: replay a captured CUDA graph per shape      */
+    int32_t use_graph;      /* 1: replay a captured CUDA graph per shape; a
+                               replay runs with the call's seed and the
+                               model's current tables, like a plain launch   */
     double deadline_s;      /* > 0: abort the kernel after this many seconds  */
 } fpt_launch;
 
