@@ -111,22 +111,23 @@ def tail_ess(ctx, prop: Proposal, model: int, n_traj: int, seed: int, run_ids, N
 def train_select(ctx, prop: Proposal, model: int, rounds: int, checkpoints, val_traj: int, val_seed: int,
                  N_tail: float, max_steps: int, dN: float, val_runs: int = 1, **train_kw) -> Proposal:
     """train() for `rounds` rounds with model selection on held-out runs: at
-    each round count c in `checkpoints` (and at the end) the current proposal
+    each round count in `checkpoints` (and at the end) the current proposal
     is run val_runs times on val_traj trajectories of Philox seed val_seed
-    (run ids 64 c + j, independent of the training runs when val_seed differs
-    from the training seed), and the parameters with the most pooled tail ESS
-    per EM step are kept and re-packed. The measurements go to
-    prop.selection."""
+    (run ids 0 .. val_runs-1, independent of the training runs when val_seed
+    differs from the training seed), and the parameters with the most pooled
+    tail ESS per EM step are kept and re-packed. Every checkpoint sees the
+    same noise (common random numbers): a rare path with a large weight then
+    weighs on all candidates alike instead of on whichever checkpoint drew
+    it. The measurements go to prop.selection."""
     import torch
-    if not 1 <= val_runs <= 64:
-        raise ValueError("val_runs must be in [1, 64]")
+    if val_runs < 1:
+        raise ValueError("val_runs must be at least 1")
     stops = sorted({int(c) for c in checkpoints if 0 < int(c) < rounds} | {rounds})
     best, best_params, done = -1.0, None, 0
     for c in stops:
         train(ctx, prop, model, rounds=c - done, first_round=done, **train_kw)
         done = c
-        v = tail_ess(ctx, prop, model, val_traj, val_seed, [64 * c + j for j in range(val_runs)], N_tail,
-                     max_steps, dN)
+        v = tail_ess(ctx, prop, model, val_traj, val_seed, list(range(val_runs)), N_tail, max_steps, dN)
         v["round"] = c
         prop.selection.append(v)
         if v["ess_per_step"] > best:

@@ -203,11 +203,10 @@ def test_train_select_keeps_the_best_checkpoint(torch):
         assert [v["round"] for v in sel] == [20, 40, 60]
         assert all(v["ess_tail"] > 0 and v["p_tail"] > 0 for v in sel)
         best = max(sel, key=lambda v: v["ess_per_step"])
-        c = best["round"]
-        again = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, [64 * c, 64 * c + 1], N_tail, m.max_steps, m.dN)
+        again = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, [0, 1], N_tail, m.max_steps, m.dN)
         # the pooled figure is the ESS of the two runs' tail sums together
-        one = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, 64 * c, N_tail, m.max_steps, m.dN)
-        two = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, 64 * c + 1, N_tail, m.max_steps, m.dN)
+        one = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, 0, N_tail, m.max_steps, m.dN)
+        two = TR.tail_ess(ctx, prop, 0, 1 << 14, 91, 1, N_tail, m.max_steps, m.dN)
     sw = one["p_tail"] * (1 << 14) + two["p_tail"] * (1 << 14)
     sw2 = (one["p_tail"] * (1 << 14)) ** 2 / one["ess_tail"] + (two["p_tail"] * (1 << 14)) ** 2 / two["ess_tail"]
     assert again["ess_tail"] == pytest.approx(sw * sw / sw2, rel=1e-9)
