@@ -45,6 +45,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "effective first-passage samples/sec at tail P(dN)<=1e-12"
+USR_MODEL_TEXT = "piecewise-linear USR, V0=2e-10 a+=1e-3 a-=1e-6, phi*=1"
 UNIT = "samples/s"
 TAIL_P = 1e-12
 
@@ -205,8 +206,10 @@ def reference_arm(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "usr_fixed_bias_tail", "proposal": f"constant A={A}",
-                       "n_traj_per_step": n, "N_tail": tail["N_12"], "table_points": 4096},
+            "config": {"workload": "usr_fixed_bias_tail", "model": USR_MODEL_TEXT,
+                       "proposal": f"constant A={A} (the paper's bias; the learned network is a GPU training product)",
+                       "n_traj_per_step": n, "N_tail": tail["N_12"], "table_points": W.USR_TABLE.n_points,
+                       "dN": m.dN, "max_steps": m.max_steps},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} trajectories per step, FP64 C oracle, OpenMP"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -697,7 +700,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "usr_learned_tail" if learned else "usr_fixed_bias_tail",
-                       "model": "piecewise-linear USR, V0=2e-10 a+=1e-3 a-=1e-6, phi*=1",
+                       "model": USR_MODEL_TEXT,
                        "proposal": "learned MLP 3-64-64-2 (bf16)" if learned else f"constant A={A_fixed}",
                        "n_traj_per_step_per_gpu": n, "N_tail": N_tail,
                        "table_points": W.USR_TABLE.n_points, "dN": m.dN, "max_steps": m.max_steps,
