@@ -122,6 +122,7 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            os.unlink(self.path)
         time.sleep(0.3)
 
     def stop(self):
@@ -133,24 +134,32 @@ class Clocks:
             self.proc.wait(5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                smax.append(float(p[2]))
-            except ValueError:
-                continue
-            for name, v in zip(names, p[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
+        with open(self.path) as f:
+            out = parse_clocks(f)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def parse_clocks(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi samples of Clocks.FIELDS (csv, noheader, nounits)."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        p = [x.strip() for x in line.split(",")]
+        if len(p) < 9:
+            continue
+        try:
+            sm.append(float(p[1]))
+            smax.append(float(p[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, p[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def measured_peaks():
