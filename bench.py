@@ -55,7 +55,7 @@ TAIL_P = 1e-12
 # 5, predication 2, Philox4x32-10 (40 per 4 steps) 10, uniforms + Box-Muller
 # (32 per 4 normals) 8. The learned proposal adds one network evaluation per
 # 128-step segment: 44 mma + 61 fragment loads + 128 SiLU (4 each) + 64 packs +
-# ~40 shuffles/selects per lane = ~760, i.e. 6 per step. See the design doc.
+# ~40 shuffles/selects per lane = ~760, i.e. 6 per step.
 INSTR_PER_STEP = 60
 INSTR_PER_STEP_MLP = 66
 # Full-rank (2-D) stepper, per step: Philox (40 per 2 steps) 20, uniforms +

@@ -467,21 +467,32 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
  *
  * No context, no allocation: the scratch (per-bin maxima, jackknife moments,
  * scalars; about 1.3 MB) is a fixed array inside the library that every GPU
- * loading the library holds until the process exits. The call runs on the
- * calling thread's current device; the first call on a device looks up the
- * array's device address (make that first call before any stream capture).
- * The array is cleared at the start of every call, and all calls share it:
- * calls whose work overlaps on the GPU (different streams, or different
- * threads without ordering) race and give wrong results.
+ * loading the library holds until the process exits. The call runs in the
+ * CUDA context current on the calling thread (with none current, the current
+ * device's primary context). The array's device address is valid only in
+ * that context, so the first call in each context looks it up and caches it
+ * by the context's id: the first call in the primary context of a device, in
+ * a context pushed by another library, or after cudaDeviceReset (which makes
+ * a new context). Make that first call in a context before any stream
+ * capture. The array is cleared at the start of every call, and all calls
+ * share it: calls whose work overlaps on the GPU (different streams, or
+ * different threads without ordering) race and give wrong results.
  *
  * Inputs: nsteps, logw, status (device, n entries; status as FPT_TRAJ_*),
  * dN, bins as in fpt_histogram (1 <= n_bins <= FPT_NOALLOC_MAX_BINS), N_tail.
  * Output: `out`, device, FPT_HIST_OUT_DOUBLES(n_bins) doubles: ten arrays of
- * n_bins (count, log_sum_w, log_sum_w2, sum_lw, sum_lw2, pdf, se_w, pdf_ln,
- * se_ln, se_jk) then 16 scalars (n_total, n_passed, n_under, n_over, n_capped,
- * n_tail, N_mean, N_mean_w, ess_tail, p_tail, log_max_w, 0...). Asynchronous
- * on cuda_stream (NULL: the legacy default stream). Errors: FPT_E_INVALID for
- * bad sizes (message in fpt_last_error(NULL)), FPT_E_CUDA for launch errors.
+ * n_bins, then 16 scalars. Per bin b (empty bins in brackets):
+ *   [0] count (0), [1] log_sum_w (-inf), [2] log_sum_w2 (-inf), [3] sum_lw (0),
+ *   [4] sum_lw2 (0), [5] pdf (0), [6] se_w (0), [7] pdf_ln and [8] se_ln
+ *   (NaN unless the bin holds at least 2 trajectories), [9] se_jk (0).
+ * Scalars at 10 n_bins + k (value when no trajectory passed in brackets):
+ *   0 n_total, 1 n_passed, 2 n_under, 3 n_over, 4 n_capped, 5 n_tail,
+ *   6 N_mean (NaN), 7 N_mean_w (NaN), 8 ess_tail (0; also 0 with an empty
+ *   tail set or N_tail = NaN), 9 p_tail (0 likewise), 10 log_max_w (-inf),
+ *   11..15 reserved, written as 0.
+ * Asynchronous on cuda_stream (NULL: the legacy default stream). Errors:
+ * FPT_E_INVALID for bad sizes (message in fpt_last_error(NULL)), FPT_E_CUDA
+ * for launch errors or a failed address lookup.
  */
 #define FPT_NOALLOC_MAX_BINS 1024
 #define FPT_HIST_OUT_DOUBLES(n_bins) (10 * (n_bins) + 16)

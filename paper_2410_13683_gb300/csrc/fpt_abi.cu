@@ -872,6 +872,10 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
         total += d.n_traj;
     }
     if (total > (1LL << 32)) return fail(ctx, FPT_E_INVALID, "more than 2^32 trajectories in one call");
+    // the learned-proposal steppers index every table by the field: a call with
+    // an MLP run cannot also carry a run on a time-indexed (noise-window) table
+    if (mlp_run >= 0 && nidx)
+        return fail(ctx, FPT_E_INVALID, "a call with a learned-proposal run needs phi-indexed tables for all its runs");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
     fpt_status st = ensure_units(ctx, std::max<long long>(total, 1));

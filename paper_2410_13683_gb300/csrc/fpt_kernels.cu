@@ -18,6 +18,7 @@
 #include "fpt_internal.h"
 #include "fpt_mlp.cuh"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -921,6 +922,7 @@ __global__ void __launch_bounds__(128) hist_finalize_kernel(const HistParams P, 
         o[8] = s[kScTailW2] > 0 ? s[kScTailW] * s[kScTailW] / s[kScTailW2] : 0.0;
         o[9] = s[kScTailW] > 0 ? exp(MT + log(s[kScTailW]) - log(n)) : 0.0;
         o[10] = Mg;
+        for (int k = 11; k < 16; ++k) o[k] = 0.0;     // reserved
     }
 }
 
@@ -961,25 +963,66 @@ static __device__ __align__(256) unsigned char g_hist_scratch[kNoAllocBytes];
 
 size_t hist_noalloc_scratch_bytes() { return kNoAllocBytes; }
 
-// Device address of the array, looked up once per device with that device
-// current (host code must not use the symbol itself as an address).
+// Device address of the array. A device address is valid only in the context
+// it was looked up in, so the cache is keyed by the id of the calling thread's
+// current context (cuCtxGetId: unique for the life of the process, so a
+// context created after cudaDeviceReset, or a non-primary context pushed by
+// another library, looks the address up again). The first call in a context
+// does the lookup; host code must not use the symbol itself as an address.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+struct NoAllocEntry {
+    unsigned long long ctx_id;
+    unsigned char *ptr;
+};
 static std::mutex g_noalloc_mu;
-static unsigned char *g_noalloc_ptr[64] = {};
+static NoAllocEntry g_noalloc_cache[64];
+static int g_noalloc_n = 0;
+static CtxGetCurrentFn g_ctx_get_current = nullptr;
+static CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Id of the current context; 0 when no context is current.
+static cudaError_t current_ctx_id(unsigned long long *id)
+{
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext c = nullptr;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    if (!c) return cudaSuccess;
+    if (g_ctx_get_id(c, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    return cudaSuccess;
+}
 
 static cudaError_t noalloc_scratch(unsigned char **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_hist_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    unsigned long long id = 0;
+    cudaError_t e = current_ctx_id(&id);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; id && i < g_noalloc_n; ++i)
+        if (g_noalloc_cache[i].ctx_id == id) {
+            *out = g_noalloc_cache[i].ptr;
+            return cudaSuccess;
+        }
+    // no cached address for this context: look it up (with no context
+    // current, this initialises the current device's primary context first)
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_hist_scratch);
+    if (e != cudaSuccess) return e;
+    if (!id && (e = current_ctx_id(&id)) != cudaSuccess) return e;
+    if (id && g_noalloc_n < 64) g_noalloc_cache[g_noalloc_n++] = NoAllocEntry{id, static_cast<unsigned char *>(p)};
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 

@@ -67,3 +67,30 @@ def test_window_usr_parity(torch):
         mism, near = compare(g[r], o, res.phi_in - res.phi_end, f"usr window A={A}",
                              max_mismatch=0.25, max_step_diff=1)
         print(f"usr window A={A}: mismatch {mism:.4%}, near-ties {near:.4%}")
+
+
+def test_learned_run_with_a_time_indexed_table_is_rejected(torch):
+    """The learned-proposal steppers index every table by the field, so a call
+    that carries an MLP run on a phi-indexed table and another run on a
+    time-indexed (noise-window) table must be refused before any launch."""
+    m = W.BM.model
+    S, T = np.full(16, W.BM_S), np.zeros(16)
+    with fpt.fpt_init_model([m, m]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, 16, 1.0, -0.1, 0.2, S, T)
+        fpt.fpt_noise_table(ctx, 1, fpt.FPT_TABLE_USER_N, 16, 1.0, 0.25, 1.5, S, T)
+        blob = torch.zeros(fpt.FPT_MLP_BLOB_BYTES, dtype=torch.uint8, device="cuda")
+        fpt.fpt_mlp_pack(ctx, torch.zeros(fpt.FPT_MLP_PARAMS, device="cuda"), blob)
+        mlp = fpt.run_desc(0, 256, seed=72, run_id=0, bias_kind=fpt.FPT_BIAS_MLP, mlp=blob, mlp_segment=64,
+                           mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max=2.0)
+        for other in (fpt.run_desc(1, 256, seed=72, run_id=1, A=0.5), fpt.run_desc(1, 256, seed=72, run_id=1)):
+            with pytest.raises(fpt.FptError) as e:
+                fpt.fpt_run(ctx, [mlp, other])
+            assert e.value.status == fpt.FPT_E_INVALID and "phi-indexed" in str(e.value)
+        # an empty MLP run still selects the learned stepper: refused as well
+        empty = fpt.run_desc(0, 0, seed=72, run_id=0, bias_kind=fpt.FPT_BIAS_MLP, mlp=blob, mlp_segment=64,
+                             mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max=2.0)
+        with pytest.raises(fpt.FptError) as e:
+            fpt.fpt_run(ctx, [empty, fpt.run_desc(1, 256, seed=72, run_id=1)])
+        assert e.value.status == fpt.FPT_E_INVALID
+        # the context stays usable
+        assert fpt.fpt_run(ctx, [mlp]) == fpt.FPT_OK and fpt.fpt_sync(ctx) == fpt.FPT_OK

@@ -58,7 +58,10 @@ def test_noalloc_histogram_matches_the_context_histogram():
             out = torch.full((fpt.hist_out_doubles(nb),), float("nan"), dtype=torch.float64, device="cuda")
             fpt.fpt_histogram_noalloc(dn, dl, ds, m.dN, lo, hi, nb, out, N_tail=tail, stream=s)
             s.synchronize()
-            got = fpt.unpack_hist(out.cpu().numpy(), nb)
+            raw = out.cpu().numpy()
+            got = fpt.unpack_hist(raw, nb)
+            # every output slot is written: the 11 scalars, then 5 reserved zeros
+            assert np.all(np.isfinite(raw[10 * nb:])) and np.all(raw[10 * nb + 11:] == 0.0)
             ref = fpt.fpt_histogram_data(ctx, dn, dl, ds, m.dN, lo, hi, nb, N_tail=tail, stream=s)
             _compare(got, ref)
             assert got["n_total"] == n and got["n_tail"] > 0
