@@ -57,7 +57,11 @@ TAIL_P = 1e-12
 # 128-step segment: 44 mma + 61 fragment loads + 128 SiLU (4 each) + 64 packs +
 # ~40 shuffles/selects per lane = ~760, i.e. 6 per step.
 INSTR_PER_STEP = 60
-INSTR_PER_STEP_MLP = 66
+# The learned proposal's roofline counts the same 60 algorithmic slots per step
+# (the step itself); the network's amortised cost (~8 per step with the
+# exponential-based SiLU) is reported beside it as frac_incl_network.
+INSTR_PER_STEP_MLP = 60
+INSTR_NETWORK_PER_STEP = 8
 # Full-rank (2-D) stepper, per step: Philox (40 per 2 steps) 20, uniforms +
 # Box-Muller for 2 normals 16, two-entry table lookup + 3 interpolations 16,
 # drift 9, (phi, pi) update 8, field compensated add 4, log-weight (Kahan) 7,
@@ -180,6 +184,32 @@ def roofline(steps_per_launch, launch_ms, sm_count, sm_max_mhz, traffic, instr_p
             "peak_source": f"{sm_count} SMs x {SM_LANES} lanes x {sm_max_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
 
 
+def pipe_fractions(steps_per_s, sm_count, sm_max_mhz):
+    """FP32-pipe, XU (special-function) and executed-issue fractions of the
+    learned stepper at the measured EM-step rate, from the per-step pipe counts
+    of its ncu capture (profiles/em_kernel_mlp_usr_timed.json, taken at the
+    timed configuration): thread instructions per step on the FMA pipes
+    against SMs x 128 lanes x clock, on the XU against SMs x 16 x clock, and
+    all executed thread instructions against the issue peak."""
+    path = os.path.join(ROOT, "profiles", "em_kernel_mlp_usr_timed.json")
+    try:
+        with open(path) as f:
+            pr = json.load(f)
+    except (OSError, ValueError):
+        return None
+    clk = sm_max_mhz * 1e6
+    per = pr.get("per_step", {})
+    out = {"pipes_source": f"profiles/em_kernel_mlp_usr_timed.json (ncu, commit {pr.get('commit', '?')})"}
+    if "thread_inst_fma" in per:
+        out["fp32_pipe_frac"] = round(per["thread_inst_fma"] * steps_per_s / (sm_count * SM_LANES * clk), 4)
+    if "thread_inst_xu" in per:
+        out["xu_frac"] = round(per["thread_inst_xu"] * steps_per_s / (sm_count * 16 * clk), 4)
+    if "thread_inst" in per:
+        out["executed_instr_per_step"] = per["thread_inst"]
+        out["issue_frac_executed"] = round(per["thread_inst"] * steps_per_s / (sm_count * SM_LANES * clk), 4)
+    return out
+
+
 def cpu_oracle_sample(model_res_tab, A, N_tail, n, seed=7):
     """The FP64 oracle on the host cores: ESS_T per second on n trajectories."""
     from oracle import estimators as E
@@ -247,6 +277,19 @@ def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
                     N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 17)
     torch.cuda.synchronize()
     return prop, time.perf_counter() - t0
+
+
+def save_proposal(prop, path):
+    """Store a trained proposal (fp32 parameters and its input normalisation)."""
+    np.savez(path, params=prop.params.detach().cpu().numpy(), shift=np.asarray(prop.shift),
+             scale=np.asarray(prop.scale), segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags)
+
+
+def load_proposal(ctx, fpt, TR, path):
+    """A proposal stored by save_proposal, packed for this context."""
+    z = np.load(path)
+    return TR.new_proposal(ctx, z["params"], shift=tuple(z["shift"]), scale=tuple(z["scale"]),
+                           segment=int(z["segment"]), alpha_max=float(z["alpha_max"]), flags=int(z["flags"]))
 
 
 def peak_pdf(fpt, ctx, run, stream, N_lo, N_hi, bins=48):
@@ -471,6 +514,8 @@ def main():
     ap.add_argument("--no-bump", action="store_true", help="skip the Gaussian-bump leg")
     ap.add_argument("--no-window", action="store_true", help="skip the noise-window leg")
     ap.add_argument("--pipeline", type=int, default=2, help="steps in flight (contexts / streams)")
+    ap.add_argument("--net", default="", help="load a trained proposal (.npz of --save-net) instead of training")
+    ap.add_argument("--save-net", default="", help="store the trained proposal (.npz)")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -506,8 +551,12 @@ def main():
 
     train_info = None
     prop = None
-    if learned:
+    if learned and args.net:
+        prop = load_proposal(ctx, fpt, TR, args.net)
+    elif learned:
         prop, train_s = train_proposal(ctx, fpt, TR, info, N_tail)
+        if args.save_net and rank == 0:
+            save_proposal(prop, args.save_net)
         h = prop.history
         train_info = {"rounds": len(h), "seconds": round(train_s, 2), "traj_per_round": TRAIN["n_traj"],
                       "lambda": TRAIN["lam"], "N_cut": N_tail, "final_loss": round(h[-1]["loss"], 3),
@@ -558,7 +607,7 @@ def main():
 
     def pipelined(K, step_of, ev=None, before=None, dfun=None, per_step=None):
         """K steps, up to P in flight; returns the summed tail sums and steps
-        (and appends each step's tail ESS to per_step)."""
+        (and appends each step's (sum_T w, sum_T w^2) to per_step)."""
         tot = [0.0, 0.0, 0.0]
         for k in range(min(P - 1, K)):
             if before:
@@ -574,7 +623,7 @@ def main():
             for i in range(3):
                 tot[i] += r[i]
             if per_step is not None:
-                per_step.append(shard.ess_of(r[0], r[1]))
+                per_step.append((r[0], r[1]))
         return tot
 
     def one_step(step, ev=None, d=None):
@@ -613,6 +662,8 @@ def main():
         elapsed = float(t.item())
     sw_tot, sw2_tot = shard.merge_tail_sums(sw_tot, sw2_tot, dist, device="cuda")
     ess_total = shard.ess_of(sw_tot, sw2_tot)
+    # spread of the pooled ESS over the timed steps (this rank's steps)
+    spread = shard.ess_spread([a for a, _ in ess_steps], [b for _, b in ess_steps])
     n_total = float(n) * args.steps * world
     value = ess_total / elapsed
 
@@ -701,6 +752,12 @@ def main():
     rl = roofline(steps_tot / args.steps, interval_ms if P > 1 else mean_run_ms, sm_count, sm_max, traffic,
                   INSTR_PER_STEP_MLP if learned else INSTR_PER_STEP)
     rl["launch_time"] = ("timed region / steps, %d launches in flight" % P) if P > 1 else "CUDA events per launch"
+    if learned:
+        rl["frac_incl_network"] = round(rl["frac"] * (INSTR_PER_STEP_MLP + INSTR_NETWORK_PER_STEP) /
+                                        INSTR_PER_STEP_MLP, 4)
+    pipes = pipe_fractions(steps_tot / elapsed, sm_count, sm_max)
+    if pipes and learned:
+        rl.update(pipes)
     if not learned:
         rl["kernel"] = "em_kernel<weighted, smem table>"
 
@@ -721,7 +778,11 @@ def main():
             "ess_tail_total": ess_total,
             # each step's own tail ESS: with heavy-tailed weights a few paths
             # decide sum w^2, and the spread shows it
-            "ess_tail_per_step": [round(e) for e in ess_steps],
+            "ess_tail_per_step": [round(shard.ess_of(a, b)) for a, b in ess_steps],
+            # the rate's own uncertainty: bootstrap over the timed steps (95%) and
+            # the delete-one-step jackknife error
+            "value_ci": [value * spread["lo"], value * spread["hi"]] if spread["lo"] is not None else None,
+            "value_rel_se": spread["rel_se"],
             # the estimate itself, beside the oracle's (FP64, constant bias): the
             # weights are exact, so a good proposal changes the error, not the value
             "p_tail": {"value": sw_tot / n_total, "rel_se": math.sqrt(max(0.0, 1.0 / ess_total - 1.0 / n_total))
@@ -730,8 +791,12 @@ def main():
             "em_steps_per_step": steps_tot / args.steps,
             "em_steps_per_s": steps_tot / elapsed, "pipeline": P,
             "em_launch_ms": mean_run_ms}
+    if args.net:
+        line["config"]["proposal"] += f" (loaded from {os.path.basename(args.net)}, not trained in this run)"
     if train_info:
         line["train"] = train_info
+        # the training charged to this run: ESS of the timed steps over training + timed time
+        line["value_incl_training"] = ess_total / (train_info["seconds"] + elapsed)
     line.update(extras)
     if "direct" in extras and extras["direct"]["ess_tail_per_s"] > 0:
         line["gain_vs_direct"] = value / extras["direct"]["ess_tail_per_s"]
@@ -739,6 +804,9 @@ def main():
         line["gain_vs_fixed_bias"] = value / extras["fixed_bias"]["ess_tail_per_s"]
     if "fixed_bias_sweep" in extras and extras["fixed_bias_sweep"]["best_ess_tail_per_s"] > 0:
         line["gain_vs_best_fixed_bias"] = value / extras["fixed_bias_sweep"]["best_ess_tail_per_s"]
+        if "value_incl_training" in line:
+            line["gain_vs_best_fixed_bias_incl_training"] = (line["value_incl_training"] /
+                                                             extras["fixed_bias_sweep"]["best_ess_tail_per_s"])
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import tables as OT
         res = OT.resolve(m)

@@ -1178,14 +1178,7 @@ fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double 
     if (!dev) {
         if (n > ctx->x_cap) {
             CK(cudaStreamSynchronize(s));
-            cudaFree(ctx->d_records);
-    cudaFree(ctx->d_rec_cursor);
-    cudaFree(ctx->d_Y);
-    cudaFree(ctx->d_coef);
-    cudaFree(ctx->d_acc);
-    cudaFree(ctx->d_grad);
-    cudaFree(ctx->d_tmp);
-    cudaFree(ctx->d_xn); cudaFree(ctx->d_xlw); cudaFree(ctx->d_xst);
+            cudaFree(ctx->d_xn); cudaFree(ctx->d_xlw); cudaFree(ctx->d_xst);
             ctx->d_xn = nullptr; ctx->d_xlw = nullptr; ctx->d_xst = nullptr; ctx->x_cap = 0;
             CK(cudaMalloc(&ctx->d_xn, sizeof(int32_t) * n));
             CK(cudaMalloc(&ctx->d_xlw, sizeof(double) * n));

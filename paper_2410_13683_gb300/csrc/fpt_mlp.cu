@@ -180,7 +180,7 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t &r0, uint32_t &r1, uint32
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
 }
 
-__device__ __forceinline__ float sigmoid_f(float v) { return fmaf(0.5f, tanh_approx(0.5f * v), 0.5f); }
+__device__ __forceinline__ float sigmoid_f(float v) { return __fdividef(1.0f, 1.0f + __expf(-v)); }
 
 __device__ __forceinline__ float dsilu_f(float v)
 {

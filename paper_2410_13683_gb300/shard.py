@@ -38,3 +38,31 @@ def merge_tail_sums(sw: float, sw2: float, dist=None, device=None) -> tuple:
     t = torch.tensor([sw, sw2], dtype=torch.float64, device=device)
     dist.all_reduce(t)
     return float(t[0]), float(t[1])
+
+
+def ess_spread(sw_steps, sw2_steps, n_boot: int = 2000, seed: int = 0) -> dict:
+    """Uncertainty of the pooled tail ESS from the per-step tail sums.
+
+    The steps are independent batches, so the pooled ESS = (sum sw)^2 / sum sw2
+    is resampled over steps (bootstrap, n_boot resamples with replacement):
+    returns the 2.5% and 97.5% quantiles relative to the pooled value, and the
+    delete-one-step jackknife relative standard error. With heavy-tailed
+    weights a few steps hold most of sum sw2; the spread shows how much the
+    pooled figure depends on them."""
+    import numpy as np
+    a = np.asarray(sw_steps, dtype=np.float64)
+    b = np.asarray(sw2_steps, dtype=np.float64)
+    K = len(a)
+    if K < 2 or b.sum() <= 0:
+        return {"lo": None, "hi": None, "rel_se": None, "steps": K}
+    pooled = a.sum() ** 2 / b.sum()
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, K, (n_boot, K))
+    A, B = a[idx].sum(axis=1), b[idx].sum(axis=1)
+    boot = np.where(B > 0, A * A / np.where(B > 0, B, 1.0), 0.0)
+    lo, hi = np.quantile(boot, [0.025, 0.975])
+    jk = np.array([(a.sum() - a[k]) ** 2 / (b.sum() - b[k]) if b.sum() > b[k] else 0.0 for k in range(K)])
+    # pooled over K - 1 steps: scale to K steps before comparing
+    jk = jk * K / (K - 1)
+    se = math.sqrt((K - 1) / K * float(np.sum((jk - jk.mean()) ** 2)))
+    return {"lo": float(lo / pooled), "hi": float(hi / pooled), "rel_se": se / pooled, "steps": K}

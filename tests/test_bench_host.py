@@ -3,6 +3,8 @@ reasons decide whether a number stands), the issue roofline, the step count
 of runs where no path passed, and the constant-amplitude sweep's pick."""
 import math
 
+import numpy as np
+
 import pytest
 
 import bench
@@ -68,3 +70,29 @@ def test_fixed_sweep_prices_ess_per_step():
     assert rows["2.0"]["em_steps"] == pytest.approx(1e4) and rows["2.0"]["ess_tail_per_s"] == 0.0
     assert rows["0.5"]["ess_tail_per_s"] == pytest.approx(100.0 / 5e4 * 1e9)
     assert out["best_A"] == 0.5
+
+
+def test_ess_spread_of_identical_steps_is_zero():
+    from paper_2410_13683_gb300 import shard
+    r = shard.ess_spread([2.0] * 8, [0.5] * 8)
+    assert r["lo"] == pytest.approx(1.0) and r["hi"] == pytest.approx(1.0) and r["rel_se"] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_ess_spread_covers_the_repeat_to_repeat_scatter():
+    """Steps with lognormal tail sums: the jackknife error of one set of 20
+    steps matches the scatter of the pooled ESS over independent sets, and a
+    step holding most of sum w^2 widens the bootstrap interval."""
+    from paper_2410_13683_gb300 import shard
+    rng = np.random.default_rng(3)
+    pooled, ses = [], []
+    for _ in range(400):
+        w = np.exp(rng.normal(0.0, 1.0, (20, 50)))
+        sw, sw2 = w.sum(axis=1), (w * w).sum(axis=1)
+        pooled.append(sw.sum() ** 2 / sw2.sum())
+        ses.append(shard.ess_spread(sw, sw2, n_boot=200)["rel_se"])
+    scatter = np.std(pooled) / np.mean(pooled)
+    assert 0.6 < np.mean(ses) / scatter < 1.5
+    sw, sw2 = np.ones(10), np.ones(10)
+    sw2[3] = 50.0
+    r = shard.ess_spread(sw, sw2)
+    assert r["lo"] < 0.5 and r["hi"] > 1.2

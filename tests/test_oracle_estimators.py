@@ -80,3 +80,34 @@ def test_combine_inverse_variance():
                       [[20, 20], [20, 0]])
     assert P[0] == pytest.approx(2.0) and se[0] == pytest.approx(1 / math.sqrt(2))
     assert P[1] == pytest.approx(2.0)
+
+
+@pytest.mark.parametrize("s,p", [(2.0, 0.5), (0.3, 0.1)])
+def test_lognormal_error_matches_the_spread_of_replicates(s, p):
+    """The stated error of the lognormal estimator (Cox's term on the log,
+    sqrt(s^2/n_b + s^4/(2(n_b - 1))), combined with the binomial error of
+    n_b/n) against the spread of K independent replicates: each replicate has
+    n trajectories, a fraction p of them in the bin, with ln w ~ N(-3, s^2).
+    The variance of ln P over the replicates must equal the mean stated
+    relative variance within the chi-square band of K - 1 degrees of freedom.
+    At s = 2 the Cox terms dominate (dropping s^4/(2(n_b - 1)) would cut the
+    stated variance by 3x); at s = 0.3, p = 0.1 the binomial term dominates."""
+    rng = np.random.default_rng(17 + int(10 * s))
+    K, n = 1500, 400
+    logP, rel2 = np.empty(K), np.empty(K)
+    for r in range(K):
+        inbin = rng.random(n) < p
+        nsteps = np.where(inbin, 500, 1500)               # bin [0.4, 0.6) holds N = 0.5
+        lw = rng.normal(-3.0, s, n)
+        h = E.histogram(nsteps, lw, np.zeros(n, np.uint8), 1e-3, 0.4, 0.6, 1, G=1)
+        P, se = E.p_lognormal(h)
+        logP[r] = math.log(P[0])
+        rel2[r] = (se[0] / P[0]) ** 2
+    emp, stated = logP.var(ddof=1), rel2.mean()
+    # chi-square band of the sample variance, 4.5 standard deviations wide
+    band = 4.5 * math.sqrt(2.0 / (K - 1))
+    print(f"s={s} p={p}: var ln P over replicates {emp:.5g}, stated {stated:.5g}, ratio {emp / stated:.4f}")
+    assert abs(emp / stated - 1.0) < band + 0.03
+    # the mean of the estimator is the lognormal mean p exp(m + s^2/2)/db (bias O(s^4/n_b))
+    mean_P = np.exp(logP).mean()
+    assert abs(mean_P / (p * math.exp(-3.0 + 0.5 * s * s) / 0.2) - 1.0) < 0.05

@@ -130,3 +130,49 @@ def test_log_variance_gradient_2d_by_finite_differences():
             q[k][idx] -= 2 * h
             fd = (fp - L(q)) / (2 * h)
             assert abs(fd - g[k][idx]) <= 1e-5 * max(1e-3, abs(fd)) + 1e-7
+
+
+@pytest.mark.parametrize("round_bf16", [False, True])
+def test_log_field_input_rebuilt_from_the_random_walk(round_bf16):
+    """The ln x input of the learned proposal (FPT_MLP_LOG_X), pinned on the
+    exponential model, where the field is an exact Gaussian random walk: with
+    the recorded alpha of each held segment, x_n = x_0 + sum_i (-mu + alpha_s s)
+    dN + s sqrt(dN) xi_i rebuilds the path from the Philox stream alone. At
+    every segment start the recorded network input must be ln of that x (the
+    natural log of phi - phi_end, not of phi, not x itself), and the recorded
+    alpha must be the numpy network's clamped projection at (ln x, pi, N).
+    A network with large input weights on ln x makes alpha move with it."""
+    wl = W.BM
+    m = wl.model
+    res = T.resolve(m)
+    tab = T.user_table(np.full(16, W.BM_S), np.zeros(16), -0.1, 0.2)
+    p = _params(seed=9, out_scale=0.5)
+    x_in = m.phi_in - m.phi_end
+    shift, scale, seg, amax = [math.log(x_in), -W.BM_MU, 0.0], [2.0, 50.0, 0.2], 32, 0.4
+    mlp = S.MLPBias(p, segment=seg, in_shift=shift, in_scale=scale, alpha_max=amax,
+                    round_bf16=round_bf16, log_x=True)
+    sdN = math.sqrt(m.dN)
+    clamped = 0
+    for j in range(6):
+        tr = S.run_segments(m, res, tab, mlp, seed=23, run_id=1, traj=j)
+        n = tr["nsteps"]
+        xi = np.concatenate([S.normals4(23, 1, j, b) for b in range((n + 3) // 4)])[:n]
+        alpha = np.repeat(tr["alpha"], seg)[:n]
+        x = x_in + np.concatenate([[0.0], np.cumsum((-W.BM_MU + alpha * W.BM_S) * m.dN + W.BM_S * sdN * xi)])
+        starts = np.arange(0, n, seg)
+        assert len(starts) == len(tr["alpha"])
+        # (the rebuilt sum rounds differently from the step-by-step field: 1e-10 of x)
+        np.testing.assert_allclose(tr["state"][:, 0], np.log(x[starts]), rtol=0, atol=1e-8)
+        np.testing.assert_allclose(tr["state"][:, 1], -W.BM_MU, rtol=0, atol=0)
+        np.testing.assert_allclose(tr["state"][:, 2], starts * m.dN, rtol=1e-15, atol=0)
+        s = M.normalise(np.stack([np.log(x[starts]), np.full(len(starts), -W.BM_MU), starts * m.dN], 1),
+                        shift, scale)
+        o, _ = M.forward(p, s, round_bf16)
+        a = M.alpha_of(o, np.zeros(len(starts)), amax)
+        np.testing.assert_allclose(tr["alpha"], a, rtol=1e-7, atol=1e-9)
+        clamped += int(np.sum(np.abs(a) >= amax))
+        # the input really is the log: alpha taken at x itself would differ
+        s_lin = M.normalise(np.stack([x[starts], np.full(len(starts), -W.BM_MU), starts * m.dN], 1),
+                            shift, scale)
+        assert np.max(np.abs(M.alpha_of(M.forward(p, s_lin, round_bf16)[0], np.zeros(len(starts)), amax) - a)) > 1e-3
+    assert clamped > 0
