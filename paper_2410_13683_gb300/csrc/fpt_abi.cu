@@ -118,6 +118,15 @@ struct fpt_ctx {
     float *d_grad = nullptr;
     float *d_tmp = nullptr;
     long long tmp_cap = 0;
+    // deterministic backward: per-block partial gradients, record order
+    float *d_gpart = nullptr;
+    uint32_t *d_perm = nullptr;
+    long long perm_cap = 0;
+    int *d_cnt = nullptr;
+    long long cnt_cap = 0;
+    long long *d_off = nullptr;
+    long long off_cap = 0;
+    int *d_rec_err = nullptr;
 };
 
 static fpt_status fail(fpt_ctx *c, fpt_status s, const std::string &msg)
@@ -180,6 +189,11 @@ static void free_all(fpt_ctx *ctx)
     cudaFree(ctx->d_acc);
     cudaFree(ctx->d_grad);
     cudaFree(ctx->d_tmp);
+    cudaFree(ctx->d_gpart);
+    cudaFree(ctx->d_perm);
+    cudaFree(ctx->d_cnt);
+    cudaFree(ctx->d_off);
+    cudaFree(ctx->d_rec_err);
     cudaFree(ctx->d_xn);
     cudaFree(ctx->d_xlw);
     cudaFree(ctx->d_xst);
@@ -1270,6 +1284,14 @@ fpt_status fpt_mlp_pack(fpt_ctx *ctx, const float *params, void *blob, void *cud
     return FPT_OK;
 }
 
+// Per-block partial gradients of the backward (fixed size per device).
+static fpt_status ensure_gpart(fpt_ctx *ctx)
+{
+    if (ctx->d_gpart) return FPT_OK;
+    CK(cudaMalloc(&ctx->d_gpart, sizeof(float) * (size_t)mlp_bwd_max_blocks(ctx->sm_count) * kMlpParams));
+    return FPT_OK;
+}
+
 fpt_status fpt_mlp_eval(fpt_ctx *ctx, const void *blob, const float *s_in, const float *tan_t, int64_t n,
                         float alpha_max, float *alpha, float *o, void *cuda_stream)
 {
@@ -1310,12 +1332,13 @@ fpt_status fpt_mlp_grad(fpt_ctx *ctx, const float *params, const float *s_in, co
     }
     fpt_status st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, 9 * n + 2 * kMlpParams);
     if (st != FPT_OK) return st;
+    if ((st = ensure_gpart(ctx)) != FPT_OK) return st;
     float *drec = ctx->d_tmp, *dd = drec + 8 * n, *dp = dd + n, *dg = dp + kMlpParams;
     CK(cudaMemcpyAsync(drec, hrec.data(), sizeof(float) * 8 * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dd, hd.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dp, hp.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dg, 0, sizeof(float) * kMlpParams, s));
-    CK(mlp_bwd_launch(dp, drec, n, nullptr, 0.0f, alpha_max, dd, dg, ctx->sm_count, s));
+    CK(mlp_bwd_launch(dp, drec, n, nullptr, 0.0f, alpha_max, dd, dg, ctx->sm_count, s, nullptr, ctx->d_gpart));
     CK(cudaMemcpyAsync(grad, dg, sizeof(float) * kMlpParams, cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
     return FPT_OK;
@@ -1339,12 +1362,13 @@ fpt_status fpt_mlp_grad2(fpt_ctx *ctx, const float *params, const float *s_in, c
     }
     fpt_status st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, 10 * n + 2 * kMlpParams);
     if (st != FPT_OK) return st;
+    if ((st = ensure_gpart(ctx)) != FPT_OK) return st;
     float *drec = ctx->d_tmp, *dd = drec + 8 * n, *dp = dd + 2 * n, *dg = dp + kMlpParams;
     CK(cudaMemcpyAsync(drec, hrec.data(), sizeof(float) * 8 * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dd, hd.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dp, hp.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dg, 0, sizeof(float) * kMlpParams, s));
-    CK(mlp_bwd_launch(dp, drec, n, nullptr, 0.0f, alpha_max, dd, dg, ctx->sm_count, s, 1));
+    CK(mlp_bwd_launch(dp, drec, n, nullptr, 0.0f, alpha_max, dd, dg, ctx->sm_count, s, nullptr, ctx->d_gpart, 1));
     CK(cudaMemcpyAsync(grad, dg, sizeof(float) * kMlpParams, cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
     return FPT_OK;
@@ -1382,11 +1406,16 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
         ctx->rec_cap = want;
     }
     if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
-    if (!ctx->d_acc) CK(cudaMalloc(&ctx->d_acc, 64));
+    if (!ctx->d_acc) CK(cudaMalloc(&ctx->d_acc, sizeof(double) * mlp_coef_scratch_doubles()));
     if (!ctx->d_grad) CK(cudaMalloc(&ctx->d_grad, sizeof(float) * kMlpParams));
+    if (!ctx->d_rec_err) CK(cudaMalloc(&ctx->d_rec_err, 64));
     fpt_status st = ensure_dev(ctx, ctx->d_coef, ctx->coef_cap, ch);
     if (st != FPT_OK) return st;
     if ((st = ensure_dev(ctx, ctx->d_Y, ctx->y_cap, ch)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_perm, ctx->perm_cap, ctx->rec_cap)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_cnt, ctx->cnt_cap, ch)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_off, ctx->off_cap, ch)) != FPT_OK) return st;
+    if ((st = ensure_gpart(ctx)) != FPT_OK) return st;
     CK(cudaMemsetAsync(ctx->d_grad, 0, sizeof(float) * kMlpParams, s));
     double sumY = 0, sumY2 = 0, sumN = 0;
     long long n_rec_total = 0, n_capped = 0, n_passed = 0;
@@ -1406,16 +1435,24 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
         CK(cudaMemcpy(&n_rec, ctx->d_rec_cursor, sizeof(n_rec), cudaMemcpyDeviceToHost));
         CK(mlp_coef_launch(ctx->d_nsteps, ctx->d_logw, sub.n_traj, m.dN, lambda, N_cut, 2.0 / (double)n_total,
                            ctx->d_Y, ctx->d_acc, ctx->d_coef, s));
+        // records in a fixed order (by trajectory, then segment), so that the
+        // gradient does not depend on the order the stepper appended them in
+        CK(rec_order_launch(ctx->d_records, (long long)n_rec, sub.n_traj, run->mlp_segment, ctx->d_cnt,
+                            ctx->d_off, ctx->d_perm, ctx->d_rec_err, s));
         CK(mlp_bwd_launch(params, ctx->d_records, (long long)n_rec, ctx->d_coef, (float)m.dN, run->alpha_max,
-                          nullptr, ctx->d_grad, ctx->sm_count, s, ctx->tables[run->model].rank2 ? 1 : 0));
+                          nullptr, ctx->d_grad, ctx->sm_count, s, ctx->d_perm, ctx->d_gpart,
+                          ctx->tables[run->model].rank2 ? 1 : 0));
         double acc[2];
+        int rec_err = 0;
         CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&rec_err, ctx->d_rec_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         // mean first-passage time of the chunk
         fpt_hist h;
         std::memset(&h, 0, sizeof(h));
         st = hist_run(ctx, ctx->d_nsteps, ctx->d_logw, ctx->d_status, 0, sub.n_traj, m.dN, 0.0,
                       (double)m.max_steps * m.dN + 1.0, 1, NAN, &h, s);
         if (st != FPT_OK) return st;
+        if (rec_err) return fail(ctx, FPT_E_STATE, "segment records out of order (code " + std::to_string(rec_err) + ")");
         sumY += acc[0];
         sumY2 += acc[1];
         sumN += h.N_mean * (double)h.n_passed;

@@ -425,9 +425,9 @@ __device__ __forceinline__ bool past_deadline(const EmParams &P, unsigned long l
 }
 
 // Close the warp's open segments at a refill point: record r holds
-// q0 = (inputs, slot 3) and q1 = (slot 4, slot 5, unit, steps), appended with
-// one warp-aggregated atomic on the record cursor; records past the buffer
-// raise flag 3 instead of being written.
+// q0 = (inputs, slot 3) and q1 = (slot 4, slot 5, unit, first step of the
+// segment), appended with one warp-aggregated atomic on the record cursor;
+// records past the buffer raise flag 3 instead of being written.
 __device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, SegRec &sg, bool active,
                                               float4 q0, float s4, float s5)
 {
@@ -444,7 +444,7 @@ __device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, 
             if (idx < P.rec_cap) {
                 float4 *q = reinterpret_cast<float4 *>(P.records + 8 * idx);
                 q[0] = q0;
-                q[1] = make_float4(s4, s5, __uint_as_float((uint32_t)L.unit), __int_as_float(L.n - sg.n0));
+                q[1] = make_float4(s4, s5, __uint_as_float((uint32_t)L.unit), __int_as_float(sg.n0));
             } else {
                 atomicExch(P.flags + 3, 1);
             }

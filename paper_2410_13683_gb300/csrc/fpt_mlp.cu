@@ -102,10 +102,18 @@ cudaError_t mlp_eval_launch(const void *blob, const float *s, const float *tan_t
 // ---------------------------------------------------------------------------
 // loss coefficients: c_j = (2/n)(Y_j - b), Y_j = ln w_j + lambda min(N_j, N_cut),
 // with b = mean Y over the run; also writes sum Y and sum Y^2 (loss monitor).
+// The sums are deterministic: each block reduces its grid-stride share in a
+// fixed order into its own partial, and one thread adds the partials in block
+// order (no floating-point atomics, so the result does not depend on timing).
 // ---------------------------------------------------------------------------
-__global__ void mlp_y_kernel(const int32_t *__restrict__ nsteps, const double *__restrict__ logw, long long n,
-                             double dN, double lambda, double N_cut, double *__restrict__ Y, double *__restrict__ acc)
+constexpr int kYBlocks = 1024;
+
+__global__ void __launch_bounds__(256) mlp_y_kernel(const int32_t *__restrict__ nsteps,
+                                                    const double *__restrict__ logw, long long n, double dN,
+                                                    double lambda, double N_cut, double *__restrict__ Y,
+                                                    double *__restrict__ part)
 {
+    __shared__ double r1[8], r2[8];
     double s1 = 0.0, s2 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double N = (double)nsteps[i] * dN;
@@ -119,9 +127,24 @@ __global__ void mlp_y_kernel(const int32_t *__restrict__ nsteps, const double *_
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(acc, s1);
-        atomicAdd(acc + 1, s2);
+        r1[threadIdx.x >> 5] = s1;
+        r2[threadIdx.x >> 5] = s2;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t1 += r1[w]; t2 += r2[w]; }
+        part[2 * blockIdx.x] = t1;
+        part[2 * blockIdx.x + 1] = t2;
+    }
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ part, int nb, double *__restrict__ acc)
+{
+    double t1 = 0.0, t2 = 0.0;
+    for (int b = 0; b < nb; ++b) { t1 += part[2 * b]; t2 += part[2 * b + 1]; }
+    acc[0] = t1;
+    acc[1] = t2;
 }
 
 __global__ void mlp_coef_kernel(const double *__restrict__ Y, long long n, const double *__restrict__ acc,
@@ -132,24 +155,111 @@ __global__ void mlp_coef_kernel(const double *__restrict__ Y, long long n, const
         coef[i] = (float)(scale * (Y[i] - mean));
 }
 
-// coef_j = scale (Y_j - mean Y); scale = 2/n of the whole round
+size_t mlp_coef_scratch_doubles() { return 2 * kYBlocks + 2; }
+
+// coef_j = scale (Y_j - mean Y); scale = 2/n of the whole round. acc holds
+// 2 kYBlocks + 2 doubles: the block partials, then (sum Y, sum Y^2).
 cudaError_t mlp_coef_launch(const int32_t *nsteps, const double *logw, long long n, double dN, double lambda,
                             double N_cut, double scale, double *Y, double *acc, float *coef, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
-    if (e != cudaSuccess) return e;
-    const int grid = (int)std::min<long long>(2048, std::max<long long>(1, (n + 255) / 256));
-    mlp_y_kernel<<<grid, 256, 0, s>>>(nsteps, logw, n, dN, lambda, N_cut, Y, acc);
+    const int grid = (int)std::min<long long>(kYBlocks, std::max<long long>(1, (n + 255) / 256));
+    double *part = acc + 2;
+    mlp_y_kernel<<<grid, 256, 0, s>>>(nsteps, logw, n, dN, lambda, N_cut, Y, part);
+    sum_partials_kernel<<<1, 1, 0, s>>>(part, grid, acc);
     mlp_coef_kernel<<<grid, 256, 0, s>>>(Y, n, acc, scale, coef);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// record order
+// ---------------------------------------------------------------------------
+// The stepper appends segment records with an atomic cursor, so their order
+// in the buffer depends on warp timing. The backward sums over records in
+// tiles, and floating-point sums depend on the order, so the records are put
+// in a fixed order first: by trajectory (launch unit), then by segment. A
+// trajectory's segments start at multiples of the segment length (the lane
+// that runs it was loaded at a refill point, and refill points are segment
+// starts), so segment k of unit u goes to position off[u] + k, off the
+// exclusive prefix sum of the per-unit counts: a permutation built by integer
+// counting and a scan, exact and independent of timing.
+__global__ void rec_count_kernel(const float *__restrict__ rec, long long n_rec, long long n_units,
+                                 int *__restrict__ cnt, int *__restrict__ err)
+{
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_rec;
+         r += (long long)gridDim.x * blockDim.x) {
+        const uint32_t u = __float_as_uint(rec[8 * r + 6]);
+        if ((long long)u < n_units) atomicAdd(cnt + u, 1);
+        else atomicOr(err, 1);
+    }
+}
+
+// Exclusive scan of cnt[0 .. n) into off (one block of 1024 threads: each
+// thread scans a contiguous slice, the slice totals are scanned in shared
+// memory, then each slice is written with its base).
+__global__ void __launch_bounds__(1024) rec_scan_kernel(const int *__restrict__ cnt, long long n,
+                                                        long long *__restrict__ off)
+{
+    __shared__ long long tot[1024];
+    const long long per = (n + blockDim.x - 1) / blockDim.x;
+    const long long b = threadIdx.x * per, e = min(n, b + per);
+    long long t = 0;
+    for (long long i = b; i < e; ++i) t += cnt[i];
+    tot[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const long long v = tot[k];
+            tot[k] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    long long run = tot[threadIdx.x];
+    for (long long i = b; i < e; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+}
+
+__global__ void rec_perm_kernel(const float *__restrict__ rec, long long n_rec, long long n_units, int segment,
+                                const int *__restrict__ cnt, const long long *__restrict__ off,
+                                uint32_t *__restrict__ perm, int *__restrict__ err)
+{
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_rec;
+         r += (long long)gridDim.x * blockDim.x) {
+        const uint32_t u = __float_as_uint(rec[8 * r + 6]);
+        const int n0 = __float_as_int(rec[8 * r + 7]);
+        if ((long long)u >= n_units || n0 < 0 || (n0 % segment) != 0) { atomicOr(err, 2); continue; }
+        const int k = n0 / segment;
+        if (k >= cnt[u]) { atomicOr(err, 4); continue; }
+        // slots start at 0xffffffff: a slot taken twice means two records of one segment
+        if (atomicExch(perm + off[u] + k, (uint32_t)r) != 0xffffffffu) atomicOr(err, 8);
+    }
+}
+
+cudaError_t rec_order_launch(const float *rec, long long n_rec, long long n_units, int segment, int *cnt,
+                             long long *off, uint32_t *perm, int *err, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n_units, s))) return e;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), s))) return e;
+    if (n_rec <= 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(perm, 0xff, sizeof(uint32_t) * (size_t)n_rec, s))) return e;
+    const int grid = (int)std::min<long long>(4096, (n_rec + 255) / 256);
+    rec_count_kernel<<<grid, 256, 0, s>>>(rec, n_rec, n_units, cnt, err);
+    rec_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_units, off);
+    rec_perm_kernel<<<grid, 256, 0, s>>>(rec, n_rec, n_units, segment, cnt, off, perm, err);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // backward over segment records
 // ---------------------------------------------------------------------------
-// Record layout (8 x 32-bit): in0, in1, in2, tan_t, raw alpha, sum_xi, unit, steps.
+// Record layout (8 x 32-bit): in0, in1, in2, tan_t, raw alpha, sum_xi, unit,
+// first step of the segment.
 // dalpha = coef[unit] * (-sqrt(dN) * sum_xi), zero where |raw alpha| >= amax.
-// Full-rank (2-D) records: in0, in1, in2, sum_xi2, 0, sum_xi1, unit, steps; the
+// Full-rank (2-D) records: in0, in1, in2, sum_xi2, 0, sum_xi1, unit, first step; the
 // output gradient is coef[unit] (-sqrt(dN)) (sum_xi1, sum_xi2), each component
 // zero where that output is clamped (beta_k = clamp(o_k)).
 constexpr int kBwdWarps = 4;
@@ -215,7 +325,8 @@ __device__ __forceinline__ void st_bf16x2(__nv_bfloat16 *p, float lo, float hi)
 __global__ void __launch_bounds__(kBwdWarps * 32)
 mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long long n_rec,
                const float *__restrict__ coef, float neg_sqrt_dN, float amax,
-               const float *__restrict__ dalpha_direct, float *__restrict__ grad, int rank2)
+               const float *__restrict__ dalpha_direct, const uint32_t *__restrict__ perm,
+               float *__restrict__ partial, int rank2)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
@@ -273,7 +384,10 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         // ---- load records of this tile
         if (tid < kBwdRows) {
-            const long long r = tile * kBwdRows + tid;
+            const long long slot = tile * kBwdRows + tid;
+            // records in a fixed order; a slot the ordering left unfilled (it
+            // reports that as an error) reads as an empty row
+            const long long r = slot < n_rec ? (perm ? (long long)perm[slot] : slot) : n_rec;
             float in0 = 0, in1 = 0, in2 = 0, tq = 0, da = 0;
             if (r < n_rec) {
                 const float *q = rec + 8 * r;
@@ -451,14 +565,19 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
     }
 
     // ---- flush: accumulator element (row g / g + 8, column 2t / 2t + 1 of each n tile)
+    // into this block's partial gradient; every parameter has exactly one
+    // writer in the block (warps own disjoint output rows of W1, W2 and disjoint
+    // column tiles of W3), so plain stores fill the whole row and the partials
+    // are summed later in block order
     const int m0 = 16 * warp;
+    float *grad = partial + (size_t)blockIdx.x * kMlpParams;
 #pragma unroll
     for (int nt = 0; nt < 9; ++nt) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int o = m0 + g + 8 * (e >> 1), c = 8 * nt + 2 * t + (e & 1);
-            if (c < kMlpH) atomicAdd(grad + kOffW2 + o * kMlpH + c, gW2[nt][e]);
-            else if (c == kMlpH) atomicAdd(grad + kOffB2 + o, gW2[nt][e]);
+            if (c < kMlpH) grad[kOffW2 + o * kMlpH + c] = gW2[nt][e];
+            else if (c == kMlpH) grad[kOffB2 + o] = gW2[nt][e];
         }
     }
 #pragma unroll
@@ -466,8 +585,8 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int o = m0 + g + 8 * (e >> 1), c = 8 * nt + 2 * t + (e & 1);
-            if (c < kMlpIn) atomicAdd(grad + kOffW1 + o * kMlpIn + c, gW1[nt][e]);
-            else if (c == kMlpIn) atomicAdd(grad + kOffB1 + o, gW1[nt][e]);
+            if (c < kMlpIn) grad[kOffW1 + o * kMlpIn + c] = gW1[nt][e];
+            else if (c == kMlpIn) grad[kOffB1 + o] = gW1[nt][e];
         }
     }
 #pragma unroll
@@ -478,26 +597,44 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
         for (int e = 0; e < 2; ++e) {                           // rows g only (outputs 0, 1)
             const int o = g, c = 8 * nt + 2 * t + e;
             if (o >= kMlpOut) continue;
-            if (c < kMlpH) atomicAdd(grad + kOffW3 + o * kMlpH + c, gW3[j][e]);
-            else if (c == kMlpH) atomicAdd(grad + kOffB3 + o, gW3[j][e]);
+            if (c < kMlpH) grad[kOffW3 + o * kMlpH + c] = gW3[j][e];
+            else if (c == kMlpH) grad[kOffB3 + o] = gW3[j][e];
         }
     }
 }
 
 size_t mlp_bwd_smem() { return sizeof(BwdSmem); }
 
+// grad[i] += sum over blocks b = 0, 1, ... of partial[b][i], in block order.
+__global__ void mlp_grad_reduce_kernel(const float *__restrict__ partial, int nb, float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    float t = 0.0f;
+    for (int b = 0; b < nb; ++b) t += partial[(size_t)b * kMlpParams + i];
+    grad[i] += t;
+}
+
+int mlp_bwd_max_blocks(int sm_count) { return 3 * sm_count; }
+
+// The gradient of a call is deterministic: records in the order perm gives
+// (nullptr: buffer order), tiles statically assigned to blocks, per-block
+// partials (partial: mlp_bwd_max_blocks(sm_count) x kMlpParams floats) added
+// in block order. grad accumulates (+=).
 cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_rec, const float *coef, float dN,
                            float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s,
-                           int rank2)
+                           const uint32_t *perm, float *partial, int rank2)
 {
     const size_t smem = sizeof(BwdSmem);
     cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (n_rec <= 0) return cudaSuccess;
     const long long tiles = (n_rec + kBwdRows - 1) / kBwdRows;
-    const int grid = (int)std::min<long long>(tiles, (long long)sm_count * 3);
+    const int grid = (int)std::min<long long>(tiles, (long long)mlp_bwd_max_blocks(sm_count));
     mlp_bwd_kernel<<<grid, kBwdWarps * 32, smem, s>>>(params, rec, n_rec, coef, -sqrtf(dN), amax,
-                                                      dalpha_direct, grad, rank2);
+                                                      dalpha_direct, perm, partial, rank2);
+    if ((e = cudaGetLastError())) return e;
+    mlp_grad_reduce_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(partial, grid, grad);
     return cudaGetLastError();
 }
 

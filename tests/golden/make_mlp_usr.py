@@ -5,7 +5,8 @@ Writes tests/golden/mlp_usr_trained.json: the fp32 parameters of a
 configuration the benchmark times -- inputs (ln x, pi, N) shifted and scaled,
 alpha held for 128-step segments, |alpha| <= 8, step cap 2^19 -- by the
 log-variance loss towards the tilted target e^{lambda min(N, N_cut)} P
-(lambda = 0.25, N_cut raised from 10 to 40 e-folds), with Adam. Everything
+(lambda = 0.25, N_cut raised from 10 to N_12 = 152.5 e-folds), with Adam, 110
+rounds of 1024 trajectories. Everything
 here runs in oracle/: the trajectories and their segment records come from the
 FP64 C stepper (oracle.stepper.run_segments, Philox seed 4004, run id = round),
 the gradient from oracle.mlp.alpha_grad (bf16 rounding of the network's
@@ -53,9 +54,9 @@ def _one(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--rounds", type=int, default=60)
-    ap.add_argument("--traj", type=int, default=512)
-    ap.add_argument("--ncut-max", type=float, default=40.0)
+    ap.add_argument("--rounds", type=int, default=110)
+    ap.add_argument("--traj", type=int, default=1024)
+    ap.add_argument("--ncut-max", type=float, default=152.5)
     args = ap.parse_args()
 
     import workloads as W

@@ -140,7 +140,7 @@ def test_learned_stepper_matches_oracle_per_trajectory(torch, setup):
     assert explained == bad.sum(), "unexplained trajectories:\n" + "\n".join(details)
     assert np.mean(~same) <= MAX_PARTED
     assert bad.mean() <= MAX_PARTED
-    # the configuration is the one timed: long tail paths, a live clamp, log-field inputs
+    # the configuration is the one timed: long tail paths with spread-out weights
     assert o["nsteps"].mean() * m.dN > 20.0
     assert np.std(o["logw"]) > 1.0
 

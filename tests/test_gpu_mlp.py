@@ -213,3 +213,27 @@ def test_train_select_keeps_the_best_checkpoint(torch):
     assert again["steps"] == pytest.approx(one["steps"] + two["steps"], rel=1e-12)
     assert again["ess_per_step"] == pytest.approx(best["ess_per_step"], rel=1e-9)
     assert again["steps"] == pytest.approx(best["steps"], rel=1e-12)
+
+
+def test_training_is_deterministic(torch):
+    """Two trainings from the same parameters on the same trajectories give
+    the same network bit for bit: segment records are put in a fixed order
+    (trajectory, segment) before the backward, per-block partial gradients are
+    added in block order and the loss sums are reduced without atomics. The
+    stepper appends the records in an order that depends on warp timing, and
+    chunks of different sizes and launch shapes change it, which must not
+    change the result."""
+    v0 = fpt.canonical_params(W.mlp_init(16, out_scale=0.2))
+    nets = []
+    for block in (384, 128):
+        with bm_ctx() as ctx:
+            fpt.fpt_set_launch(ctx, block=block)
+            prop = TR.new_proposal(ctx, v0, shift=(0.025, -0.01, 3.0), scale=(40.0, 100.0, 0.3),
+                                   segment=64, alpha_max=4.0)
+            TR.train(ctx, prop, 0, rounds=4, n_traj=1 << 13, seed=19, lam=9.5, N_cut=lambda r: 1e9, lr=1e-2)
+            nets.append((prop.params.cpu().numpy().copy(), [h["loss"] for h in prop.history],
+                         [h["grad_norm"] for h in prop.history]))
+    (p1, l1, g1), (p2, l2, g2) = nets
+    assert np.array_equal(p1.view(np.uint32), p2.view(np.uint32))
+    assert l1 == l2 and g1 == g2
+    assert not np.array_equal(p1, v0)
