@@ -121,7 +121,9 @@ typedef struct {
     double A;            /* constant amplitude */
     int64_t segment;     /* MLP: alpha recomputed every `segment` steps */
     double alpha_max;    /* MLP: |alpha| clamp */
-    int32_t round_bf16;  /* MLP: round operands to bfloat16 as the GPU does */
+    int32_t round_bf16;  /* MLP: bfloat16 network -- inputs and hidden activations rounded
+                            to bfloat16 here; the weights W1..W3 come already rounded
+                            (oracle/stepper.py MLPBias), the biases as given */
     int32_t log_x;       /* MLP: first input ln(max(phi - phi_end, 1e-30)) */
     const double *W1, *b1, *W2, *b2, *W3, *b3;   /* row-major (out, in) */
     double in_shift[3], in_scale[3];             /* input = (s - shift) * scale */

@@ -57,17 +57,22 @@ def bf16(x):
 
 
 def forward(p, s, round_bf16=False):
-    """s: [n, 3] normalised inputs. Returns (o [n, 2], cache)."""
+    """s: [n, 3] normalised inputs. Returns (o [n, 2], cache).
+
+    round_bf16: the network as bf16 tensor-core tiles hold it -- the weight
+    matrices W1, W2, W3 rounded to bfloat16 (biases stay fp32), and the inputs
+    and hidden activations rounded to bfloat16 before each product."""
+    W = {k: (bf16(p[k]) if round_bf16 else p[k]) for k in ("W1", "W2", "W3")}
     x = bf16(s) if round_bf16 else s
-    a1 = x @ p["W1"].T + p["b1"]
+    a1 = x @ W["W1"].T + p["b1"]
     h1 = silu(a1)
     if round_bf16:
         h1 = bf16(h1)
-    a2 = h1 @ p["W2"].T + p["b2"]
+    a2 = h1 @ W["W2"].T + p["b2"]
     h2 = silu(a2)
     if round_bf16:
         h2 = bf16(h2)
-    o = h2 @ p["W3"].T + p["b3"]
+    o = h2 @ W["W3"].T + p["b3"]
     return o, (x, a1, h1, a2, h2)
 
 

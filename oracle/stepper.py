@@ -152,11 +152,17 @@ def model_struct(m, phi_in, pi_in, phi_end) -> _Model:
 
 
 class MLPBias:
-    """FP64 MLP proposal parameters for the oracle (weights kept alive here)."""
+    """FP64 MLP proposal parameters for the oracle (weights kept alive here).
+
+    round_bf16: the network as bf16 tensor-core tiles hold it. The weight
+    matrices W1, W2, W3 are rounded to bfloat16 here, once (biases stay as
+    given), and the C forward rounds the inputs and hidden activations."""
 
     def __init__(self, params: dict, segment: int, in_shift, in_scale, alpha_max=20.0,
                  round_bf16=True, log_x=False):
-        self.p = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in params.items()}
+        from . import mlp as _mlp
+        self.p = {k: np.ascontiguousarray(_mlp.bf16(v) if (round_bf16 and k.startswith("W")) else v,
+                                          dtype=np.float64) for k, v in params.items()}
         self.segment = int(segment)
         self.in_shift = list(in_shift)
         self.in_scale = list(in_scale)
