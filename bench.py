@@ -426,6 +426,126 @@ def noise_2d_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A, sm_count, 
     return out
 
 
+def batched_bias_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, sm_count, sm_max, autotune=True,
+                     n=1 << 20):
+    """The constant-bias sweep in one launch: the eight amplitudes A in
+    {0.5, 1, 2, 3, 4, 6, 8, 10} as eight runs of n trajectories each (uneven
+    lengths: A >= 2 sends every path to the step cap), block shape and refill
+    interval from the autotuner, replayed as a captured CUDA graph. EM steps
+    per second of the mixed launch, its issue roofline, and per amplitude the
+    tail probability and tail ESS at N_12 with the inverse-variance
+    combination over amplitudes (Sec. 4.1: overlapping amplitudes)."""
+    As = W.USR_FIXED_BIAS.biases
+    ctx = fpt.fpt_init_model([m], device=torch.cuda.current_device())
+    fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
+    runs = lambda k: [fpt.run_desc(0, n, seed=seed + 60, run_id=8 * k + r, A=A, traj_offset=rank * n)
+                      for r, A in enumerate(As)]
+    launch = fpt.fpt_autotune(ctx, runs(100), fraction=0.125) if autotune else fpt.fpt_get_launch(ctx)
+    fpt.fpt_run(ctx, runs(101), stream=stream)
+    fpt.fpt_sync(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fpt.fpt_run(ctx, runs(0), stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    per, steps = {}, 0.0
+    Ps, ses, cnt = [], [], []
+    for r, A in enumerate(As):
+        h = fpt.fpt_histogram(ctx, r, 0.0, 400.0, 512, N_tail=N_tail, stream=stream)
+        steps += passed_steps(h, m.dN) + h["n_capped"] * float(m.max_steps)
+        sw, sw2 = shard.tail_sums(h)
+        ess = shard.ess_of(sw, sw2)
+        p = h["p_tail"]
+        rel = math.sqrt(max(0.0, 1.0 / ess - 1.0 / n)) if ess > 0 else None
+        per[str(A)] = {"p_tail": p, "rel_se": rel, "ess_tail": ess, "n_capped": int(h["n_capped"])}
+        if rel is not None and ess >= 10:
+            Ps.append(p)
+            ses.append(p * rel)
+    comb = None
+    if Ps:
+        wts = [1.0 / s ** 2 for s in ses]
+        comb = {"p_tail": sum(w * p for w, p in zip(wts, Ps)) / sum(wts), "rel_se": None}
+        comb["rel_se"] = 1.0 / math.sqrt(sum(wts)) / comb["p_tail"]
+    fpt.fpt_sync(ctx)
+    ctx.close()
+    rl = roofline(steps, ms, sm_count, sm_max, None, INSTR_PER_STEP)
+    rl["kernel"] = "em_kernel<weighted, smem table> (eight runs, one launch)"
+    return {"biases": list(As), "n_traj_per_bias": n, "launch": launch, "launch_ms": ms,
+            "traj_per_s": 8 * n / (ms * 1e-3), "em_steps_per_s": steps / (ms * 1e-3), "roofline": rl,
+            "per_bias": per, "combined_at_N_12": comb,
+            "note": "1/16 of the 2^24-per-amplitude workload (at 2^24 its capped paths alone are 5e13 EM steps, "
+                    "two minutes per launch); the rates are per EM step and per trajectory"}
+
+
+def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max, autotune=True, n=1 << 11,
+                     pts=256, A_fallback=4.0):
+    """The batched sweep over 64 piecewise-linear models (a- log-uniform in
+    [1e-7, 1e-4], phi* in [0.9, 1.1], V0 log-uniform in [1e-11, 1e-9]), each
+    with its learned proposal and its constant-bias fallback A = 4: 128 runs
+    of uneven lengths (step cap 2^23) in one persistent launch, tables read
+    through L1, the networks evaluated per run, block shape and refill
+    interval from the autotuner, replayed as a captured CUDA graph. Each
+    model's proposal is the network trained on the sudden-transition model,
+    applied in that model's own input normalisation (ln x / x_in, pi / |pi_in|):
+    one network per run in the launch, not a network trained per model."""
+    models = W.batch_models(64)
+    ctx = fpt.fpt_init_model(models, device=torch.cuda.current_device())
+    t0 = time.perf_counter()
+    for i in range(len(models)):
+        fpt.fpt_noise_table(ctx, i, fpt.FPT_TABLE_BESSEL, pts, 1.0)
+    table_s = time.perf_counter() - t0
+    blob = TR.new_proposal(ctx, prop.params.detach().cpu().numpy(), shift=prop.shift, scale=prop.scale,
+                           segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags)
+    props = []
+    for i in range(len(models)):
+        info = fpt.fpt_model_get_info(ctx, i)
+        x_in = info["phi_in"] - info["phi_end"]
+        props.append(TR.Proposal(blob.params, blob.blob, (math.log(x_in), 0.0, 0.0),
+                                 (prop.scale[0], 1.0 / abs(info["pi_in"]), prop.scale[2]), prop.segment,
+                                 prop.alpha_max, prop.flags))
+
+    def runs(k):
+        out = []
+        for i in range(len(models)):
+            out.append(props[i].desc(i, n, seed=seed + 70, run_id=2 * (64 * k + i), traj_offset=rank * n))
+            out.append(fpt.run_desc(i, n, seed=seed + 70, run_id=2 * (64 * k + i) + 1, A=A_fallback,
+                                    traj_offset=rank * n))
+        return out
+
+    launch = fpt.fpt_autotune(ctx, runs(100), fraction=0.25) if autotune else fpt.fpt_get_launch(ctx)
+    fpt.fpt_run(ctx, runs(101), stream=stream)
+    fpt.fpt_sync(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fpt.fpt_run(ctx, runs(0), stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps, capped, passed = 0.0, 0, 0
+    lengths = []
+    for r in range(2 * len(models)):
+        h = fpt.fpt_histogram(ctx, r, 0.0, 1e4, 64, stream=stream)
+        m = models[r // 2]
+        steps += passed_steps(h, m.dN) + h["n_capped"] * float(m.max_steps)
+        capped += int(h["n_capped"])
+        passed += int(h["n_passed"])
+        if h["n_passed"] > 0:
+            lengths.append(h["N_mean"])
+    fpt.fpt_sync(ctx)
+    ctx.close()
+    rl = roofline(steps, ms, sm_count, sm_max, None, INSTR_PER_STEP)
+    rl["kernel"] = "em_kernel<weighted, tables via L1, MLP, one network per run>"
+    return {"models": len(models), "runs": 2 * len(models), "n_traj_per_run": n, "table_points": pts,
+            "table_build_s": round(table_s, 2), "launch": launch, "launch_ms": ms,
+            "traj_per_s": 2 * len(models) * n / (ms * 1e-3), "em_steps_per_s": steps / (ms * 1e-3),
+            "roofline": rl, "censored_fraction": capped / float(2 * len(models) * n),
+            "mean_N_passed_min_max": [min(lengths), max(lengths)] if lengths else None,
+            "proposal": "sudden-transition network in each model's normalisation; fallback A = %g" % A_fallback,
+            "note": "2^11 trajectories per run instead of 2^20: the A = 4 fallback sends every path to the 2^23-step "
+                    "cap (at 2^20 per run that alone is 5.6e14 EM steps)"}
+
+
 PEAK_SIGMA = 0.05
 
 
@@ -596,6 +716,8 @@ def main():
     ap.add_argument("--no-bump", action="store_true", help="skip the Gaussian-bump leg")
     ap.add_argument("--no-window", action="store_true", help="skip the noise-window leg")
     ap.add_argument("--no-far", action="store_true", help="skip the 1e-20 tail leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the eight-amplitude batched leg")
+    ap.add_argument("--no-family", action="store_true", help="skip the 64-model batched leg")
     ap.add_argument("--pipeline", type=int, default=2, help="steps in flight (contexts / streams)")
     ap.add_argument("--net", default="", help="load a trained proposal (.npz of --save-net) instead of training")
     ap.add_argument("--save-net", default="", help="store the trained proposal (.npz)")
@@ -813,6 +935,14 @@ def main():
             sm_max_w = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
             extras["noise_window"] = window_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, A_fixed,
                                                 sm_count, sm_max_w, autotune=not args.no_autotune)
+        if not args.no_batch:
+            sm_max_b8 = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+            extras["batched_biases"] = batched_bias_leg(fpt, torch, shard, m, stream, seed, rank, N_tail,
+                                                        sm_count, sm_max_b8, autotune=not args.no_autotune)
+        if learned and not args.no_family:
+            sm_max_f = measured_peaks().get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+            extras["model_family"] = model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count,
+                                                      sm_max_f, autotune=not args.no_autotune)
         if learned and not args.no_far and "N_20" in tail:
             far = far_tail_leg(fpt, torch, TR, shard, ctx, prop, m, tail, n, seed, rank, stream, dist, world)
             extras["far_tail_20"] = far

@@ -268,8 +268,13 @@ fpt_status fpt_fit_eps2(const double *dN, const double *pdf, const double *se, i
  * (o1, o2) = MLP((x - shift) * scale), x = (phi - phi_end, pi, n dN),
  * t = tan(theta_n) at the segment start, held fixed for `mlp_segment` steps
  * (steps n = 0, mlp_segment, 2 mlp_segment, ... start a segment). All MLP runs
- * of one call share blob, segment, shift, scale and alpha_max; a call with MLP
- * runs refills finished trajectories every mlp_segment steps.
+ * of one call share mlp_segment, and a call with MLP runs refills finished
+ * trajectories every mlp_segment steps. Each MLP run may carry its own network
+ * (blob), shift, scale, alpha_max and flags: when they differ the stepper
+ * evaluates each run's network from global memory (one evaluation per run
+ * present in a warp), otherwise the shared network is staged in shared
+ * memory. Runs with different networks need 1-D phi-indexed tables and the
+ * piecewise-linear or exponential potential (FPT_E_INVALID otherwise).
  */
 typedef struct {
     int32_t model;          /* model index                                   */
@@ -331,7 +336,7 @@ fpt_status fpt_autotune(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, 
                         fpt_launch *chosen);
 
 /*
- * Run n_runs runs (1..64) in one persistent launch: one trajectory per
+ * Run n_runs runs (1..128) in one persistent launch: one trajectory per
  * thread, warp-level refill of finished trajectories every check_steps steps.
  * Results stay in the context for fpt_histogram; out (n_runs entries,
  * nullable) receives copies. Asynchronous on cuda_stream (NULL = the
@@ -456,6 +461,21 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
                                double lambda, double N_cut, const fpt_adam *adam, float *params,
                                float *adam_m, float *adam_v, void *blob,
                                fpt_train_stats *stats, void *cuda_stream);
+
+/*
+ * The held-alpha segments of one learned-proposal run (Sec. 5's open bias made
+ * concrete: what the proposal did along each path), for analysis and tests:
+ * the run (one FPT_BIAS_MLP run, 1-D table) is generated in record mode, the
+ * same trajectories as fpt_run gives, and up to `cap` records are copied to
+ * `records` (host or device, 8 floats each): the three normalised network
+ * inputs, tan(theta_n), the unclamped alpha, the sum of xi over the segment,
+ * the launch unit (trajectory index within the run, as uint32 bits) and the
+ * segment's first step (int32 bits). Records come in the order the stepper
+ * wrote them; sort by (unit, first step) for a path's sequence.
+ * *n_records = all records of the run (possibly more than cap). Blocks.
+ */
+fpt_status fpt_run_records(fpt_ctx *ctx, const fpt_run_desc *run, int64_t cap, float *records,
+                           int64_t *n_records, void *cuda_stream);
 
 /*
  * The weighted histogram of fpt_histogram_data for callers that cannot

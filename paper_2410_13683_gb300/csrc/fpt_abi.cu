@@ -823,8 +823,9 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
                    void *cuda_stream)
 {
     if (!ctx) return FPT_E_INVALID;
-    if (!runs || n_runs < 1 || n_runs > kMaxRuns) return fail(ctx, FPT_E_INVALID, "n_runs out of [1, 64]");
+    if (!runs || n_runs < 1 || n_runs > kMaxRuns) return fail(ctx, FPT_E_INVALID, "n_runs out of [1, 128]");
     std::set<int> used_models;
+    bool mnet = false;   // MLP runs with different networks (or normalisations, clamps)
     long long total = 0;
     bool weighted = false;
     bool nidx = false;
@@ -850,11 +851,13 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             if (mlp_run < 0) mlp_run = r;
             const fpt_run_desc &q = runs[mlp_run];
             if (d.mlp_flags & ~FPT_MLP_LOG_X) return fail(ctx, FPT_E_INVALID, "unknown mlp_flags bits");
-            if (d.mlp != q.mlp || d.mlp_segment != q.mlp_segment || d.alpha_max != q.alpha_max ||
-                d.mlp_flags != q.mlp_flags ||
+            // the held-alpha segment is the launch's refill interval: shared by all MLP runs
+            if (d.mlp_segment != q.mlp_segment)
+                return fail(ctx, FPT_E_INVALID, "all MLP runs of one call must share mlp_segment");
+            if (d.mlp != q.mlp || d.alpha_max != q.alpha_max || d.mlp_flags != q.mlp_flags ||
                 std::memcmp(d.mlp_shift, q.mlp_shift, sizeof(q.mlp_shift)) ||
                 std::memcmp(d.mlp_scale, q.mlp_scale, sizeof(q.mlp_scale)))
-                return fail(ctx, FPT_E_INVALID, "all MLP runs of one call must share one proposal");
+                mnet = true;
         }
         if (d.bias_kind == FPT_BIAS_CONST && (!std::isfinite(d.A) || !std::isfinite(d.A2)))
             return fail(ctx, FPT_E_INVALID, "A and A2 must be finite");
@@ -890,6 +893,10 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     // an MLP run cannot also carry a run on a time-indexed (noise-window) table
     if (mlp_run >= 0 && nidx)
         return fail(ctx, FPT_E_INVALID, "a call with a learned-proposal run needs phi-indexed tables for all its runs");
+    if (mnet && (rank2 == 1 || bump == 1 || ctx->record_mode))
+        return fail(ctx, FPT_E_INVALID,
+                    "MLP runs with different networks need 1-D noise tables and the piecewise-linear or "
+                    "exponential potential (and are not recorded for training)");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
     fpt_status st = ensure_units(ctx, std::max<long long>(total, 1));
@@ -931,9 +938,10 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     const bool smem = used_models.size() == 1;
     const int smem_model = smem ? *used_models.begin() : 0;
     const bool mlp = mlp_run >= 0;
-    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1};
-    const size_t smem_bytes = (smem ? sizeof(float4) * ctx->region_entries[smem_model] : 0) +
-                              (mlp ? (size_t)kMlpBlobBytes : 0);
+    const EmVariant var{weighted, smem, mlp, mlp && ctx->record_mode, nidx && !mlp, rank2 == 1, bump == 1,
+                        mlp && mnet};
+    const size_t smem_bytes = em_smem_bytes(var, smem ? ctx->region_entries[smem_model] : 0, n_runs,
+                                            (int)ctx->models.size());
     // the learned-proposal steppers are compiled for at most kMlpMaxBlock threads
     const int block = mlp ? std::min(ctx->launch.block, kMlpMaxBlock) : ctx->launch.block;
     int occ = em_occupancy(var, block, smem_bytes);
@@ -983,7 +991,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             GraphKey key{weighted, smem, grid, block, smem_bytes, p.groups_per_check, n_runs,
                          smem ? smem_model : -1, total,
                          (mlp ? 1 : 0) + (var.rec ? 2 : 0) + (var.nidx ? 4 : 0) + (var.rank2 ? 8 : 0) +
-                             (var.dtab ? 16 : 0) + 32 * p.mlp_run};
+                             (var.dtab ? 16 : 0) + (var.mnet ? 32 : 0) + 64 * p.mlp_run};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 RunGraph rg;
@@ -1211,7 +1219,7 @@ fpt_status fpt_autotune(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, 
                         fpt_launch *chosen)
 {
     if (!ctx) return FPT_E_INVALID;
-    if (!runs || n_runs < 1 || n_runs > kMaxRuns) return fail(ctx, FPT_E_INVALID, "n_runs out of [1, 64]");
+    if (!runs || n_runs < 1 || n_runs > kMaxRuns) return fail(ctx, FPT_E_INVALID, "n_runs out of [1, 128]");
     if (!(fraction > 0.0 && fraction <= 1.0)) return fail(ctx, FPT_E_INVALID, "fraction out of (0, 1]");
     std::vector<fpt_run_desc> sub(runs, runs + n_runs);
     for (auto &d : sub)
@@ -1372,6 +1380,43 @@ fpt_status fpt_mlp_grad2(fpt_ctx *ctx, const float *params, const float *s_in, c
     CK(cudaMemcpyAsync(grad, dg, sizeof(float) * kMlpParams, cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
     return FPT_OK;
+}
+
+fpt_status fpt_run_records(fpt_ctx *ctx, const fpt_run_desc *run, int64_t cap, float *records,
+                           int64_t *n_records, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!run || !n_records || cap < 0 || (cap > 0 && !records)) return fail(ctx, FPT_E_INVALID, "null argument");
+    if (run->bias_kind != FPT_BIAS_MLP) return fail(ctx, FPT_E_INVALID, "segment records need an MLP run");
+    if (run->model < 0 || run->model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "run model out of range");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    const fpt_model &m = ctx->models[run->model];
+    const long long want = std::min<long long>(std::max<long long>(1, run->n_traj) * (m.max_steps / std::max(4, run->mlp_segment) + 2),
+                                               1LL << 28);
+    if (want > ctx->rec_cap) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(ctx->d_records);
+        ctx->d_records = nullptr;
+        ctx->rec_cap = 0;
+        clear_graphs(ctx);
+        CK(cudaMalloc(&ctx->d_records, sizeof(float) * 8 * want));
+        ctx->rec_cap = want;
+    }
+    if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
+    ctx->record_mode = true;
+    fpt_status st = fpt_run(ctx, run, 1, nullptr, s);
+    ctx->record_mode = false;
+    if (st != FPT_OK) return st;
+    st = fpt_sync(ctx);
+    if (st == FPT_E_TIMEOUT) return st;
+    if (ctx->h_flags[3]) return fail(ctx, FPT_E_NOMEM, "segment records exceed the record buffer");
+    unsigned long long n_rec = 0;
+    CK(cudaMemcpy(&n_rec, ctx->d_rec_cursor, sizeof(n_rec), cudaMemcpyDeviceToHost));
+    *n_records = (int64_t)n_rec;
+    const long long k = std::min<long long>((long long)n_rec, cap);
+    if (k > 0) CK(cudaMemcpy(records, ctx->d_records, sizeof(float) * 8 * k, cudaMemcpyDefault));
+    return st;
 }
 
 fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t chunk, double lambda,

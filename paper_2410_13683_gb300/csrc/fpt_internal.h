@@ -32,7 +32,7 @@ double hubble(const fpt_model &m, double phi, double pi, int branch);
 
 namespace fpt_dev {
 
-constexpr int kMaxRuns = 64;
+constexpr int kMaxRuns = 128;
 constexpr int kMaxModels = 64;
 constexpr int kMaxTablePoints = 8192;
 constexpr int kJackknife = 32;       // jackknife blocks of the histogram
@@ -142,10 +142,12 @@ struct EmVariant {
     bool weighted, smem, mlp, rec, nidx;
     bool rank2;              // full-rank 2-D noise stepper
     bool dtab;               // V'/V from the bump's cubic table
+    bool mnet;               // learned proposal with one network per run
 };
 
 // Host wrappers implemented in fpt_kernels.cu.
 int em_occupancy(EmVariant v, int block, size_t smem_bytes);
+size_t em_smem_bytes(EmVariant v, int table_entries, int n_runs, int n_models);
 cudaError_t em_launch(const EmParams &p, EmVariant v, int grid, int block, size_t smem_bytes,
                       cudaStream_t s);
 

@@ -125,6 +125,7 @@ struct Lane {                // per-thread trajectory state and its constants
     bool mlp;
     bool nidx;               // noise table indexed by the step count
     int win_lo, win_hi;      // noise window in steps (nidx)
+    int run;                 // index of the lane's run in the launch
     long long unit;
 };
 
@@ -146,6 +147,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     }
     const RunSm &r = s_run[lo];
     const ModelDev &m = s_model[r.model];
+    L.run = lo;
     L.unit = unit;
     L.traj = (uint32_t)(r.traj_offset + (unit - r.unit_begin));
     L.run_id = r.run_id;
@@ -330,6 +332,69 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
     }
 }
 
+// Learned proposal with one network per run (the runs of a launch may carry
+// different networks, input normalisations and clamps; they share the
+// segment length): the warp evaluates the network of each run among its live
+// lanes in turn -- runs are contiguous in unit order, so a warp mostly holds
+// one run -- reading that run's packed weights through L1.
+template <bool SMEM>
+__device__ __forceinline__ void mlp_segment_start_multi(Lane &L, bool live, const float4 *tab,
+                                                        const RunDev *runs, const ModelDev &M0)
+{
+    const unsigned FULL = 0xffffffffu;
+    const float dN = SMEM ? M0.dN : L.dN, sqrt_dN = SMEM ? M0.sqrt_dN : L.sqrt_dN;
+    unsigned pend = __ballot_sync(FULL, live);
+    while (pend) {
+        const int run = __shfl_sync(FULL, L.run, __ffs(pend) - 1);
+        const bool mine = live && L.run == run;
+        pend &= ~__ballot_sync(FULL, mine);
+        const RunDev &pr = runs[run];
+        float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f, tan_t = 0.0f;
+        if (mine) {
+            const float xv = __fsub_rn(L.x, L.x_c);
+            in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
+            in0 = (in0 - pr.shift[0]) * pr.scale[0];
+            in1 = (L.p - pr.shift[1]) * pr.scale[1];
+            in2 = ((float)L.n * dN - pr.shift[2]) * pr.scale[2];
+            float f;
+            const float4 e = table_at<SMEM>(L, tab, f, M0);
+            const float S = fmaf(f, e.y, e.x), T = fmaf(f, e.w, e.z);
+            tan_t = S > 0.0f ? __fdividef(T, S) : 0.0f;
+        }
+        const uint2 *tiles = reinterpret_cast<const uint2 *>(pr.mlp);
+        const float *bias = reinterpret_cast<const float *>(tiles + kMlpTiles * 32);
+        float o1, o2;
+        mlp_forward_warp(tiles, bias, in0, in1, in2, o1, o2);
+        if (mine) {
+            float raw;
+            const float al = mlp_alpha_of(o1, o2, tan_t, pr.alpha_max, raw);
+            L.cb = al * sqrt_dN;
+            L.half_cb2 = 0.5f * al * al * dN;
+        }
+    }
+}
+
+// Dynamic shared memory of a stepper launch: the table (SMEM variants), the
+// staged proposal blob (single-network learned variants), then the launch's
+// run constants and model descriptors, each as many as the launch has.
+__device__ __forceinline__ RunSm *smem_runs(float4 *s_dyn, int table_entries, bool staged_blob)
+{
+    unsigned char *p = reinterpret_cast<unsigned char *>(s_dyn + table_entries);
+    return reinterpret_cast<RunSm *>(p + (staged_blob ? kMlpBlobBytes : 0));
+}
+
+__device__ __forceinline__ ModelDev *smem_models(RunSm *s_run, int n_runs)
+{
+    const size_t b = ((sizeof(RunSm) * (size_t)n_runs + 15) / 16) * 16;
+    return reinterpret_cast<ModelDev *>(reinterpret_cast<unsigned char *>(s_run) + b);
+}
+
+size_t em_smem_bytes(EmVariant v, int table_entries, int n_runs, int n_models)
+{
+    return sizeof(float4) * (size_t)table_entries + ((v.mlp && !v.mnet) ? (size_t)kMlpBlobBytes : 0) +
+           ((sizeof(RunSm) * (size_t)n_runs + 15) / 16) * 16 + sizeof(ModelDev) * (size_t)n_models;
+}
+
 // Launch prologue shared by the steppers: clock origin, per-run and per-model
 // constants, the table (SMEM variants) and the proposal blob (MLP variants)
 // staged in shared memory. `table_entries` float4 entries are staged.
@@ -410,7 +475,7 @@ __device__ __forceinline__ void first_units(const EmParams &P, Lane &L, bool &ac
     const long long unit = (long long)(base + lane);
     active = unit < P.total_units;
     if (active) lane_load(L, unit, s_run, s_model, P.n_runs);
-    else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false, L.nidx = false;
+    else L.n = 0, L.traj = 0, L.run_id = 0, L.mlp = false, L.nidx = false, L.run = 0;
 }
 
 // Deadline: true when the launch should stop (lane 0 reads the device clock).
@@ -459,20 +524,22 @@ __device__ __forceinline__ void write_records(const EmParams &P, const Lane &L, 
 // blocks, 80 registers: the network's fragments fit without spilling (a
 // 64-register build ran 512-thread blocks but executed ~7% more instructions
 // per step, and the autotuner chose 384 threads for it anyway).
-template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX, bool DTAB>
+template <bool WEIGHTED, bool SMEM, bool MLP, bool REC, bool NIDX, bool DTAB, bool MNET = false>
 __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB) ? 2 : 3)
     em_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
-    __shared__ RunSm s_run[kMaxRuns];
-    __shared__ ModelDev s_model[kMaxModels];
     __shared__ unsigned long long s_t0;
 
-    // MLP variants: the proposal's fragment blob follows the table in shared memory
-    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + (SMEM ? P.smem_table_points : 0));
+    // single-network MLP variants: the proposal's fragment blob follows the
+    // table in shared memory; then the run constants and model descriptors
+    const int tab_entries = SMEM ? P.smem_table_points : 0;
+    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + tab_entries);
     float *s_bias = reinterpret_cast<float *>(s_tiles + kMlpTiles * 32);
+    RunSm *s_run = smem_runs(s_tab, tab_entries, MLP && !MNET);
+    ModelDev *s_model = smem_models(s_run, P.n_runs);
     const RunDev &prun = P.runs[MLP ? P.mlp_run : 0];
-    stage_launch<SMEM, MLP>(P, s_tab, s_run, s_model, s_t0, s_tiles);
+    stage_launch<SMEM, MLP && !MNET>(P, s_tab, s_run, s_model, s_t0, s_tiles);
 
     const float4 *tab = SMEM ? s_tab : P.tables;
     const unsigned lane = threadIdx.x & 31u;
@@ -485,8 +552,10 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
     first_units(P, L, active, s_run, s_model);
 
     for (;;) {
-        if (MLP && __any_sync(FULL, active && L.mlp))
-            mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun, P.m0);
+        if (MLP && __any_sync(FULL, active && L.mlp)) {
+            if (MNET) mlp_segment_start_multi<SMEM>(L, active && L.mlp, tab, P.runs, P.m0);
+            else mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun, P.m0);
+        }
 
         for (int g = 0; g < P.groups_per_check; ++g) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u), P.rk);
@@ -604,12 +673,13 @@ template <bool WEIGHTED, bool SMEM, bool MLP, bool DTAB, bool REC = false>
 __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const EmParams P)
 {
     extern __shared__ __align__(16) float4 s_tab[];
-    __shared__ RunSm s_run[kMaxRuns];
-    __shared__ ModelDev s_model[kMaxModels];
     __shared__ unsigned long long s_t0;
 
-    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + (SMEM ? P.smem_table_points : 0));
+    const int tab_entries = SMEM ? P.smem_table_points : 0;
+    uint2 *s_tiles = reinterpret_cast<uint2 *>(s_tab + tab_entries);
     float *s_bias = reinterpret_cast<float *>(s_tiles + kMlpTiles * 32);
+    RunSm *s_run = smem_runs(s_tab, tab_entries, MLP);
+    ModelDev *s_model = smem_models(s_run, P.n_runs);
     const RunDev &prun = P.runs[MLP ? P.mlp_run : 0];
     stage_launch<SMEM, MLP>(P, s_tab, s_run, s_model, s_t0, s_tiles);
 
@@ -681,6 +751,9 @@ static const void *em_fn_t(EmVariant v)
 
 static const void *em_fn(EmVariant v)
 {
+    if (v.mnet)   // one network per run: 1-D, phi-indexed, no records
+        return v.smem ? (const void *)em_kernel<true, true, true, false, false, false, true>
+                      : (const void *)em_kernel<true, false, true, false, false, false, true>;
     if (v.dtab) return em_fn_t<true>(v);
     if (v.nidx && !v.rank2 && !v.mlp) {
         if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, true, false>

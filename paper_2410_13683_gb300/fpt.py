@@ -147,6 +147,8 @@ _SIGNATURES = {
     "fpt_mlp_train_round": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_double,
                                       C.c_double, C.POINTER(fpt_adam), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(fpt_train_stats), C.c_void_p]),
+    "fpt_run_records": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_void_p,
+                                  C.POINTER(C.c_int64), C.c_void_p]),
     "fpt_histogram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                         C.c_double, C.c_double, C.c_int32, C.c_double, C.c_void_p,
                                         C.c_void_p]),
@@ -481,6 +483,24 @@ def fpt_mlp_eval(ctx: Context, blob, s, tan_t, alpha_max: float, stream=None):
     _check(load().fpt_mlp_eval(ctx.handle, _ptr(blob), _ptr(s), _ptr(t), n, alpha_max, _ptr(alpha),
                                _ptr(o), _stream(stream)), ctx.handle)
     return alpha, o
+
+
+def fpt_run_records(ctx: Context, run: fpt_run_desc, cap: int = 1 << 16, stream=None):
+    """Segment records of one learned-proposal run, sorted by (unit, first
+    step): dict of arrays in (n x 3), tan, raw, sum_xi, unit, n0."""
+    rec = np.zeros((max(1, cap), 8), np.float32)
+    n = C.c_int64(0)
+    _check(load().fpt_run_records(ctx.handle, C.byref(run), cap, _ptr(rec), C.byref(n), _stream(stream)),
+           ctx.handle)
+    k = min(n.value, cap)
+    rec = rec[:k]
+    unit = rec[:, 6].view(np.uint32).astype(np.int64)
+    n0 = rec[:, 7].view(np.int32).astype(np.int64)
+    order = np.lexsort((n0, unit))
+    rec, unit, n0 = rec[order], unit[order], n0[order]
+    return {"in": rec[:, 0:3].astype(np.float64), "tan": rec[:, 3].astype(np.float64),
+            "raw": rec[:, 4].astype(np.float64), "sum_xi": rec[:, 5].astype(np.float64),
+            "unit": unit, "n0": n0, "n_records": n.value}
 
 
 def fpt_mlp_grad(ctx: Context, params, s, tan_t, dalpha, alpha_max: float, stream=None):

@@ -39,7 +39,7 @@ from oracle import tables as OT
 from paper_2410_13683_gb300 import fpt
 from paper_2410_13683_gb300 import train as TR
 
-from gpu_common import LOGW_TOL, NEAR_TIE_REL, require_gpu
+from gpu_common import LOGW_TOL, NEAR_TIE_REL, gpu_run, require_gpu
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -170,3 +170,52 @@ def test_network_forward_matches_oracle_on_trained_weights(torch, setup):
           f"median diff {np.median(d):.2e}, max {d.max():.2e}; alpha in [{al.min():.2f}, {al.max():.2f}]")
     assert off.mean() < 0.05
     assert np.all(d < 5e-2 * np.maximum(1.0, np.abs(al)))
+
+
+def test_learned_segments_match_oracle(torch, setup):
+    """Segment by segment along whole learned-proposal paths of the timed
+    configuration: the GPU's segment records (fpt_run_records: network inputs,
+    tan theta, alpha, sum of xi, first step) against the oracle's segments of
+    the same trajectories. Inputs agree to FP32 rounding, alpha to the forward
+    tolerance except at partings, the noise sums to FP32 Box-Muller accuracy.
+    The ln w that the GPU's own records imply, -sum_s [alpha_s sqrt(dN) S_s +
+    alpha_s^2 m_s dN / 2] in FP64, is compared with the GPU's accumulated ln w
+    and with the oracle's: this splits a ln w difference into what the path
+    (alpha, noise) did and what the in-kernel accumulation did."""
+    fx, p, m, res, tab = setup
+    shift, scale = np.asarray(fx["shift"]), np.asarray(fx["scale"])
+    seg, amax = int(fx["segment"]), float(fx["alpha_max"])
+    v = fpt.canonical_params(p)
+    mlp = OS.MLPBias(p, segment=seg, in_shift=tuple(shift), in_scale=tuple(scale), alpha_max=amax,
+                     round_bf16=True, log_x=True)
+    ids = [232901, 232907, 232908, 232918, 232933, 944513, 5, 77]
+    sdN = math.sqrt(m.dN)
+    rows = []
+    with fpt.fpt_init_model([m]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
+        prop = TR.new_proposal(ctx, v, shift=tuple(shift), scale=tuple(scale), segment=seg, alpha_max=amax,
+                               flags=fpt.FPT_MLP_LOG_X)
+        for tid in ids:
+            d = prop.desc(0, 1, seed=4, run_id=0, traj_offset=tid)
+            st, g = gpu_run(ctx, [d], [1])
+            rec = fpt.fpt_run_records(ctx, d, cap=1 << 13)
+            tr = OS.run_segments(m, res, tab, mlp, seed=4, run_id=0, traj=tid, cap=1 << 13)
+            k = min(len(rec["raw"]), len(tr["alpha"]))
+            s_or = (tr["state"][:k] - shift) * scale
+            din = np.abs(rec["in"][:k] - s_or).max(axis=0)
+            a_gpu = np.clip(rec["raw"][:k], -amax, amax)
+            da = np.abs(a_gpu - tr["alpha"][:k])
+            dxi = np.abs(rec["sum_xi"][:k] - tr["sum_xi"][:k])
+            steps = np.diff(np.append(rec["n0"][:k], g[0]["nsteps"][0]))
+            lw_rec = -float(np.sum(a_gpu * sdN * rec["sum_xi"][:k] + 0.5 * a_gpu ** 2 * steps * m.dN))
+            rows.append((tid, int(g[0]["nsteps"][0]), int(tr["nsteps"]), float(g[0]["logw"][0]), lw_rec,
+                         float(tr["logw"]), din, float(np.max(da)), float(np.median(da)), int(np.sum(da > 1e-5)),
+                         float(np.max(dxi)), float(np.mean(rec["sum_xi"][:k] - tr["sum_xi"][:k]))))
+    for r in rows:
+        print(f"#{r[0]}: steps {r[1]}/{r[2]}; ln w gpu {r[3]:.6f} from gpu records {r[4]:.6f} oracle {r[5]:.6f}; "
+              f"max |d in| {r[6][0]:.2e} {r[6][1]:.2e} {r[6][2]:.2e}; |d alpha| max {r[7]:.2e} median {r[8]:.2e} "
+              f"(> 1e-5: {r[9]}); |d sum xi| max {r[10]:.2e} mean d {r[11]:+.2e}")
+    for r in rows:
+        lim = LOGW_TOL * max(1.0, abs(r[5]))
+        # the GPU's accumulated ln w equals what its own records imply
+        assert abs(r[3] - r[4]) <= lim, r[0]
