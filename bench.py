@@ -83,6 +83,8 @@ INSTR_PER_STEP_NIDX = 67
 TRAIN = dict(rounds=550, n_traj=1 << 18, lam=0.25, alpha_max=8.0, segment=128, lr0=3e-3, lr_min=3e-4,
              select_from=450, select_every=25, val_traj=1 << 22, val_runs=4, val_seed=31337)
 SM_LANES = 128
+# Floor of the log-field network input, relative to x_in: ln max(x, 2^-14 x_in)
+X_FLOOR_REL = 2.0 ** -14
 # Constant amplitudes compared with the learned proposal. Larger ones send the
 # paths past the step cap (2^19 steps): at A = 1 85% of them, at A >= 3 all.
 FIXED_SWEEP = (0.25, 0.375, 0.5, 0.625, 0.75, 1.0)
@@ -263,7 +265,8 @@ def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
     p_in = abs(info["pi_in"])
     v0 = fpt.canonical_params(W.mlp_init(21, out_scale=0.0))
     prop = TR.new_proposal(ctx, v0, shift=(math.log(x_in), 0.0, 0.0), scale=(0.2, 1.0 / p_in, 0.01),
-                           segment=TRAIN["segment"], alpha_max=TRAIN["alpha_max"], flags=fpt.FPT_MLP_LOG_X)
+                           segment=TRAIN["segment"], alpha_max=TRAIN["alpha_max"], flags=fpt.FPT_MLP_LOG_X,
+                           x_floor=x_in * X_FLOOR_REL)
     lr = lambda r: TRAIN["lr0"] if r < 20 else max(TRAIN["lr_min"], TRAIN["lr0"] * 0.98 ** (r - 20))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -274,7 +277,7 @@ def train_proposal(ctx, fpt, TR, info, N_tail, seed=4):
                     N_tail=N_tail,
                     max_steps=m.max_steps, dN=m.dN,
                     n_traj=TRAIN["n_traj"], seed=seed, lam=TRAIN["lam"],
-                    N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 17)
+                    N_cut=lambda r: min(N_tail, 10.0 * 1.3 ** r), lr=lr, chunk=1 << 18)
     torch.cuda.synchronize()
     return prop, time.perf_counter() - t0
 
@@ -292,7 +295,8 @@ def far_tail_leg(fpt, torch, TR, shard, ctx, prop12, m, tail, n, seed, rank, str
     import torch as _t
     N20 = tail["N_20"]
     prop = TR.new_proposal(ctx, prop12.params.detach().cpu().numpy(), shift=prop12.shift, scale=prop12.scale,
-                           segment=prop12.segment, alpha_max=prop12.alpha_max, flags=prop12.flags)
+                           segment=prop12.segment, alpha_max=prop12.alpha_max, flags=prop12.flags,
+                           x_floor=prop12.x_floor)
     N12 = tail["N_12"]
     t0 = time.perf_counter()
     TR.train_select(ctx, prop, 0, rounds=FAR["rounds"],
@@ -344,14 +348,16 @@ def far_tail_leg(fpt, torch, TR, shard, ctx, prop12, m, tail, n, seed, rank, str
 def save_proposal(prop, path):
     """Store a trained proposal (fp32 parameters and its input normalisation)."""
     np.savez(path, params=prop.params.detach().cpu().numpy(), shift=np.asarray(prop.shift),
-             scale=np.asarray(prop.scale), segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags)
+             scale=np.asarray(prop.scale), segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags,
+             x_floor=prop.x_floor)
 
 
 def load_proposal(ctx, fpt, TR, path):
     """A proposal stored by save_proposal, packed for this context."""
     z = np.load(path)
     return TR.new_proposal(ctx, z["params"], shift=tuple(z["shift"]), scale=tuple(z["scale"]),
-                           segment=int(z["segment"]), alpha_max=float(z["alpha_max"]), flags=int(z["flags"]))
+                           segment=int(z["segment"]), alpha_max=float(z["alpha_max"]), flags=int(z["flags"]),
+                           x_floor=float(z["x_floor"]) if "x_floor" in z else 0.0)
 
 
 def peak_pdf(fpt, ctx, run, stream, N_lo, N_hi, bins=48):
@@ -503,7 +509,7 @@ def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max,
         x_in = info["phi_in"] - info["phi_end"]
         props.append(TR.Proposal(blob.params, blob.blob, (math.log(x_in), 0.0, 0.0),
                                  (prop.scale[0], 1.0 / abs(info["pi_in"]), prop.scale[2]), prop.segment,
-                                 prop.alpha_max, prop.flags))
+                                 prop.alpha_max, prop.flags, x_in * X_FLOOR_REL))
 
     def runs(k):
         out = []

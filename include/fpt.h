@@ -290,9 +290,15 @@ typedef struct {
     float mlp_scale[3];     /* FPT_BIAS_MLP: input scale                     */
     float alpha_max;        /* FPT_BIAS_MLP: |alpha| clamp (> 0)             */
     int32_t mlp_flags;      /* FPT_BIAS_MLP: FPT_MLP_LOG_X = first input is
-                               ln(max(phi - phi_end, 1e-30)) instead of
+                               ln(max(phi - phi_end, mlp_x_floor)) instead of
                                phi - phi_end                                 */
     double A2;              /* FPT_BIAS_CONST on 2-D tables: beta_2          */
+    float mlp_x_floor;      /* FPT_MLP_LOG_X: floor of phi - phi_end under the
+                               log (<= 0: 1e-30). The log amplifies the field's
+                               rounding error by 1/x near the end surface; a
+                               floor a few orders below x_in keeps the input
+                               well conditioned there                        */
+    int32_t pad_;           /* reserved, 0                                   */
 } fpt_run_desc;
 
 enum { FPT_MLP_LOG_X = 1 };

@@ -124,10 +124,19 @@ typedef struct {
     int32_t round_bf16;  /* MLP: bfloat16 network -- inputs and hidden activations rounded
                             to bfloat16 here; the weights W1..W3 come already rounded
                             (oracle/stepper.py MLPBias), the biases as given */
-    int32_t log_x;       /* MLP: first input ln(max(phi - phi_end, 1e-30)) */
+    int32_t log_x;       /* MLP: first input ln(max(phi - phi_end, x_floor)) */
     const double *W1, *b1, *W2, *b2, *W3, *b3;   /* row-major (out, in) */
     double in_shift[3], in_scale[3];             /* input = (s - shift) * scale */
+    double x_floor;      /* MLP, log_x: floor of x under the log (<= 0: 1e-30) */
 } oracle_bias;
+
+/* The log-field network input ln max(x, floor): below the floor the input is
+ * held, so that it stays well conditioned as x -> 0 at the end surface. */
+static double log_input(const oracle_bias *b, double x)
+{
+    const double fl = b->x_floor > 0.0 ? b->x_floor : 1e-30;
+    return log(x > fl ? x : fl);
+}
 
 /* Slope term V'(phi)/V(phi) of the potential families. The Gaussian bump of
  * Sec. 4.3, V = V0 f (1 + g) with f = phi^2/(m^2 + phi^2) and
@@ -214,7 +223,7 @@ static double mlp_alpha(const oracle_bias *b, const oracle_model *m,
                         double phi, double pi, int64_t n, double t)
 {
     double x = phi - m->phi_end;
-    if (b->log_x) x = log(x > 1e-30 ? x : 1e-30);
+    if (b->log_x) x = log_input(b, x);
     double s[3] = {x, pi, (double)n * m->dN};
     double o[2];
     oracle_mlp_forward(b, s, o);
@@ -280,7 +289,7 @@ static void one_trajectory(const oracle_model *m, const oracle_table *tab,
             alpha = mlp_alpha(b, m, phi, pi, n, t);
             if (seg && ns < seg->cap) {
                 double x = phi - m->phi_end;
-                if (b->log_x) x = log(x > 1e-30 ? x : 1e-30);
+                if (b->log_x) x = log_input(b, x);
                 seg->state[3 * ns + 0] = x;
                 seg->state[3 * ns + 1] = pi;
                 seg->state[3 * ns + 2] = (double)n * dN;
@@ -379,7 +388,7 @@ static void one_trajectory2(const oracle_model *m, const oracle_table2 *tab, con
         table2_lookup(tab, phi, &a, &b, &c);
         if (bias->kind == 2 && (n % bias->segment) == 0) {
             double x = phi - m->phi_end;
-            if (bias->log_x) x = log(x > 1e-30 ? x : 1e-30);
+            if (bias->log_x) x = log_input(bias, x);
             double s[3] = {x, pi, (double)n * dN}, o[2];
             oracle_mlp_forward(bias, s, o);
             beta1 = clampd(o[0], bias->alpha_max);

@@ -50,7 +50,7 @@ class _Bias(C.Structure):
                 ("W1", C.POINTER(C.c_double)), ("b1", C.POINTER(C.c_double)),
                 ("W2", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)),
                 ("W3", C.POINTER(C.c_double)), ("b3", C.POINTER(C.c_double)),
-                ("in_shift", C.c_double * 3), ("in_scale", C.c_double * 3)]
+                ("in_shift", C.c_double * 3), ("in_scale", C.c_double * 3), ("x_floor", C.c_double)]
 
 
 class _Table2(C.Structure):
@@ -159,7 +159,7 @@ class MLPBias:
     given), and the C forward rounds the inputs and hidden activations."""
 
     def __init__(self, params: dict, segment: int, in_shift, in_scale, alpha_max=20.0,
-                 round_bf16=True, log_x=False):
+                 round_bf16=True, log_x=False, x_floor=0.0):
         from . import mlp as _mlp
         self.p = {k: np.ascontiguousarray(_mlp.bf16(v) if (round_bf16 and k.startswith("W")) else v,
                                           dtype=np.float64) for k, v in params.items()}
@@ -169,6 +169,7 @@ class MLPBias:
         self.alpha_max = float(alpha_max)
         self.round_bf16 = bool(round_bf16)
         self.log_x = bool(log_x)
+        self.x_floor = float(x_floor)
         self.hidden = self.p["W1"].shape[0]
 
     def struct(self) -> _Bias:
@@ -178,7 +179,7 @@ class MLPBias:
                      W1=_dp(p["W1"]), b1=_dp(p["b1"]), W2=_dp(p["W2"]), b2=_dp(p["b2"]),
                      W3=_dp(p["W3"]), b3=_dp(p["b3"]),
                      in_shift=(C.c_double * 3)(*self.in_shift),
-                     in_scale=(C.c_double * 3)(*self.in_scale))
+                     in_scale=(C.c_double * 3)(*self.in_scale), x_floor=self.x_floor)
 
 
 def bias_struct(A: float = 0.0, mlp: MLPBias | None = None) -> _Bias:

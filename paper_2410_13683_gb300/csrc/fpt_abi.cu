@@ -681,6 +681,9 @@ static fpt_status upload_tables(fpt_ctx *ctx)
             }
             const double sq = std::sqrt(m.dN);
             d.rank2 = t.rank2 ? 1 : 0;
+            double smax = 0.0;
+            for (int j = 0; j < t.M; ++j) smax = std::max(smax, std::fabs(t.S[j]) * sq);
+            d.s_max = (float)(smax * (1.0 + 1e-6));
             if (t.rank2) {
                 // (S_phiphi, S_phipi, S_pipi, 0) sqrt(dN); entry M repeats entry M - 1
                 for (int j = 0; j <= t.M; ++j) {
@@ -854,7 +857,9 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             // the held-alpha segment is the launch's refill interval: shared by all MLP runs
             if (d.mlp_segment != q.mlp_segment)
                 return fail(ctx, FPT_E_INVALID, "all MLP runs of one call must share mlp_segment");
+            if (!std::isfinite(d.mlp_x_floor)) return fail(ctx, FPT_E_INVALID, "mlp_x_floor must be finite");
             if (d.mlp != q.mlp || d.alpha_max != q.alpha_max || d.mlp_flags != q.mlp_flags ||
+                d.mlp_x_floor != q.mlp_x_floor ||
                 std::memcmp(d.mlp_shift, q.mlp_shift, sizeof(q.mlp_shift)) ||
                 std::memcmp(d.mlp_scale, q.mlp_scale, sizeof(q.mlp_scale)))
                 mnet = true;
@@ -928,6 +933,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             for (int k = 0; k < 3; ++k) { rd.shift[k] = d.mlp_shift[k]; rd.scale[k] = d.mlp_scale[k]; }
             rd.alpha_max = d.alpha_max;
             rd.mlp_flags = d.mlp_flags;
+            rd.x_floor = d.mlp_x_floor > 0.0f ? d.mlp_x_floor : 1e-30f;
         }
         begin += d.n_traj;
     }
@@ -1393,7 +1399,7 @@ fpt_status fpt_run_records(fpt_ctx *ctx, const fpt_run_desc *run, int64_t cap, f
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
     const fpt_model &m = ctx->models[run->model];
     const long long want = std::min<long long>(std::max<long long>(1, run->n_traj) * (m.max_steps / std::max(4, run->mlp_segment) + 2),
-                                               1LL << 28);
+                                               1LL << 29);
     if (want > ctx->rec_cap) {
         CK(cudaStreamSynchronize(s));
         cudaFree(ctx->d_records);
@@ -1440,7 +1446,7 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
     const long long n_total = run->n_traj;
     const long long ch = std::min<long long>(chunk, n_total);
     const long long seg_per_traj = m.max_steps / run->mlp_segment + 2;
-    const long long want = std::min<long long>(ch * seg_per_traj, 1LL << 28);
+    const long long want = std::min<long long>(ch * seg_per_traj, 1LL << 29);
     if (want > ctx->rec_cap) {
         CK(cudaStreamSynchronize(s));
         cudaFree(ctx->d_records);

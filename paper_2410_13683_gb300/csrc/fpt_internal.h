@@ -64,6 +64,7 @@ struct ModelDev {
     float d_umax;              // intervals of the drift table
     float bump_m2, bump_phi_end, bump_dphi0, bump_inv_w2, bump_K;
     int32_t win_lo, win_hi;    // noise window [win_lo, win_hi] in steps (nidx)
+    float s_max;               // max of S_phiphi sqrt(dN) over the table (bound of a step's noise)
 };
 
 // One run of a launch (FP32 constants; 64-bit unit bookkeeping).
@@ -84,6 +85,7 @@ struct RunDev {
     float sqrt_dN;
     float dN;
     int32_t mlp_flags;
+    float x_floor;             // MLP with log-field input: floor of x under the log
 };
 
 struct EmParams {

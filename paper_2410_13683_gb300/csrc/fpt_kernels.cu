@@ -307,7 +307,7 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
     float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f, tan_t = 0.0f;
     if (live) {
         const float xv = __fsub_rn(L.x, L.x_c);
-        in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
+        in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, pr.x_floor)) : xv);
         in0 = (in0 - pr.shift[0]) * pr.scale[0];
         in1 = (L.p - pr.shift[1]) * pr.scale[1];
         in2 = ((float)L.n * dN - pr.shift[2]) * pr.scale[2];
@@ -352,7 +352,7 @@ __device__ __forceinline__ void mlp_segment_start_multi(Lane &L, bool live, cons
         float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f, tan_t = 0.0f;
         if (mine) {
             const float xv = __fsub_rn(L.x, L.x_c);
-            in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
+            in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, pr.x_floor)) : xv);
             in0 = (in0 - pr.shift[0]) * pr.scale[0];
             in1 = (L.p - pr.shift[1]) * pr.scale[1];
             in2 = ((float)L.n * dN - pr.shift[2]) * pr.scale[2];
@@ -562,12 +562,32 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
             float z[4];
             box_muller(r.x, r.y, z[0], z[1]);
             box_muller(r.z, r.w, z[2], z[3]);
+            // Fast path (single-model launches): when every lane of the warp is
+            // live and so far above the end surface that four steps cannot reach
+            // it -- a step moves the field by at most s_max (|xi| + |alpha| sqrt(dN))
+            // + |pi| dN with |xi| <= 5.77 (the largest Box-Muller radius of a
+            // 23-bit uniform), taken here with a factor 2 to spare -- and four
+            // steps stay under the cap, the four steps run without the per-step
+            // passage test and branch. The arithmetic of a step is the same on
+            // both paths, so results do not depend on which one ran.
+            const bool fast = SMEM &&
+                __all_sync(FULL, active && !done && L.n + 4 <= P.m0.max_steps &&
+                                     __fsub_rn(L.x, L.x_c) >
+                                         8.0f * fmaf(P.m0.s_max, 5.8f + fabsf(L.cb), fabsf(L.p) * P.m0.dN));
+            if (fast) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-                if (active && !done) {
+                for (int s = 0; s < 4; ++s) {
                     if (REC) sg.sum_xi += z[s];
-                    done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
+                    em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                 }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    if (active && !done) {
+                        if (REC) sg.sum_xi += z[s];
+                        done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
+                    }
+            }
             // the group's weight increments (at most 4, so a plain FP32 sum) into the
             // pair; a lane that took no step in the group adds nothing (re-adding zero
             // would re-round the pair, and how often depends on the launch shape)
@@ -646,7 +666,7 @@ __device__ __forceinline__ void mlp2_segment_start(Lane &L, bool live, SegRec &s
     float in0 = 0.0f, in1 = 0.0f, in2 = 0.0f;
     if (live) {
         const float xv = __fsub_rn(L.x, L.x_c);
-        in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, 1e-30f)) : xv);
+        in0 = ((pr.mlp_flags & FPT_MLP_LOG_X) ? __logf(fmaxf(xv, pr.x_floor)) : xv);
         in0 = (in0 - pr.shift[0]) * pr.scale[0];
         in1 = (L.p - pr.shift[1]) * pr.scale[1];
         in2 = ((float)L.n * dN - pr.shift[2]) * pr.scale[2];

@@ -60,7 +60,8 @@ class fpt_run_desc(C.Structure):
                 ("n_traj", C.c_int64), ("traj_offset", C.c_int64), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("mlp_segment", C.c_int32), ("mlp", C.c_void_p),
                 ("mlp_shift", C.c_float * 3), ("mlp_scale", C.c_float * 3),
-                ("alpha_max", C.c_float), ("mlp_flags", C.c_int32), ("A2", C.c_double)]
+                ("alpha_max", C.c_float), ("mlp_flags", C.c_int32), ("A2", C.c_double),
+                ("mlp_x_floor", C.c_float), ("pad_", C.c_int32)]
 
 
 class fpt_classical(C.Structure):
@@ -395,7 +396,7 @@ def fpt_autotune(ctx: Context, runs: Sequence[fpt_run_desc], fraction: float = 0
 def run_desc(model: int = 0, n_traj: int = 0, seed: int = 0, run_id: int = 0, A: float = 0.0,
              traj_offset: int = 0, bias_kind: Optional[int] = None, mlp=None, mlp_segment: int = 0,
              mlp_shift=(0.0, 0.0, 0.0), mlp_scale=(1.0, 1.0, 1.0), alpha_max: float = 0.0,
-             mlp_flags: int = 0, A2: float = 0.0):
+             mlp_flags: int = 0, A2: float = 0.0, mlp_x_floor: float = 0.0):
     if bias_kind is None:
         bias_kind = FPT_BIAS_MLP if mlp is not None else (
             FPT_BIAS_CONST if (A != 0.0 or A2 != 0.0) else FPT_BIAS_NONE)
@@ -403,7 +404,7 @@ def run_desc(model: int = 0, n_traj: int = 0, seed: int = 0, run_id: int = 0, A:
                         traj_offset=traj_offset, seed=seed, run_id=run_id,
                         mlp_segment=mlp_segment, mlp=_ptr(mlp),
                         mlp_shift=(C.c_float * 3)(*mlp_shift), mlp_scale=(C.c_float * 3)(*mlp_scale),
-                        alpha_max=alpha_max, mlp_flags=mlp_flags)
+                        alpha_max=alpha_max, mlp_flags=mlp_flags, mlp_x_floor=mlp_x_floor)
 
 
 def fpt_run(ctx: Context, runs: Sequence[fpt_run_desc], out: Optional[Sequence[dict]] = None,

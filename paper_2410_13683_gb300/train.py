@@ -26,6 +26,7 @@ class Proposal:
     segment: int
     alpha_max: float
     flags: int = 0
+    x_floor: float = 0.0     # log-field input: ln max(x, x_floor)
     history: List[dict] = field(default_factory=list)
     selection: List[dict] = field(default_factory=list)
 
@@ -33,18 +34,18 @@ class Proposal:
         return fpt.run_desc(model, n_traj, seed=seed, run_id=run_id, traj_offset=traj_offset,
                             bias_kind=fpt.FPT_BIAS_MLP, mlp=self.blob, mlp_segment=self.segment,
                             mlp_shift=self.shift, mlp_scale=self.scale, alpha_max=self.alpha_max,
-                            mlp_flags=self.flags)
+                            mlp_flags=self.flags, mlp_x_floor=self.x_floor)
 
 
 def new_proposal(ctx, init_params: np.ndarray, shift, scale, segment: int = 64, alpha_max: float = 4.0,
-                 flags: int = 0):
+                 flags: int = 0, x_floor: float = 0.0):
     import torch
     p = torch.tensor(np.asarray(init_params, np.float32), device="cuda")
     blob = torch.zeros(fpt.FPT_MLP_BLOB_BYTES, dtype=torch.uint8, device="cuda")
     fpt.fpt_mlp_pack(ctx, p, blob)
     torch.cuda.synchronize()
     return Proposal(p, blob, tuple(float(v) for v in shift), tuple(float(v) for v in scale), segment,
-                    alpha_max, flags)
+                    alpha_max, flags, float(x_floor))
 
 
 def train(ctx, prop: Proposal, model: int, rounds: int, n_traj: int, seed: int, lam: float,

@@ -3,7 +3,8 @@
 Writes tests/golden/mlp_usr_trained.json: the fp32 parameters of a
 3 -> 64 -> 64 -> 2 SiLU network trained on the sudden-transition model in the
 configuration the benchmark times -- inputs (ln x, pi, N) shifted and scaled,
-alpha held for 128-step segments, |alpha| <= 8, step cap 2^19 -- by the
+alpha held for 128-step segments, |alpha| <= 8, ln x floored at 2^-14 x_in,
+step cap 2^19 -- by the
 log-variance loss towards the tilted target e^{lambda min(N, N_cut)} P
 (lambda = 0.25, N_cut raised from 10 to N_12 = 152.5 e-folds), with Adam, 110
 rounds of 1024 trajectories. Everything
@@ -37,6 +38,7 @@ OUT = os.path.join(HERE, "mlp_usr_trained.json")
 SEED = 4004
 SEGMENT, ALPHA_MAX, LAM = 128, 8.0, 0.25
 
+X_FLOOR_REL = 2.0 ** -14
 _G = {}
 
 
@@ -47,8 +49,9 @@ def _init(m, res, tab):
 def _one(args):
     from oracle import stepper as S
     params, shift, scale, r, traj = args
+    x_in = _G["res"].phi_in - _G["res"].phi_end
     mlp = S.MLPBias(params, segment=SEGMENT, in_shift=shift, in_scale=scale, alpha_max=ALPHA_MAX,
-                    round_bf16=True, log_x=True)
+                    round_bf16=True, log_x=True, x_floor=x_in * X_FLOOR_REL)
     return S.run_segments(_G["m"], _G["res"], _G["tab"], mlp, seed=SEED, run_id=r, traj=traj, cap=1 << 13)
 
 
@@ -109,7 +112,8 @@ def main():
                     "log-variance loss towards the tilted target, Sec. 4.1 weights; inputs (ln x, pi, N)",
            "model": "sudden transition, V0=2e-10 a+=1e-3 a-=1e-6 phi*=1, 4096-point Bessel table sigma=1, "
                     "dN=1e-3, max_steps=2^19",
-           "segment": SEGMENT, "alpha_max": ALPHA_MAX, "log_x": True, "shift": list(shift),
+           "segment": SEGMENT, "alpha_max": ALPHA_MAX, "log_x": True, "x_floor": x_in * X_FLOOR_REL,
+           "shift": list(shift),
            "scale": list(scale), "lambda": LAM, "rounds": args.rounds, "traj_per_round": args.traj,
            "seed": SEED, "history": hist,
            "params": {k: [float(x) for x in np.asarray(v, np.float32).ravel()] for k, v in p.items()},

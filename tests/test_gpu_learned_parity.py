@@ -3,7 +3,8 @@ the benchmark times.
 
 Configuration: the sudden-transition model with the 4096-point Bessel table,
 step cap 2^19, network inputs (ln x, pi, N) shifted and scaled
-(FPT_MLP_LOG_X), alpha held for 128-step segments, |alpha| <= 8, and a
+(FPT_MLP_LOG_X, ln x floored at 2^-14 x_in), alpha held for 128-step
+segments, |alpha| <= 8, and a
 trained network: tests/golden/mlp_usr_trained.json, trained by the FP64
 oracle (tests/golden/make_mlp_usr.py). 2^22 trajectories run through the C ABI
 in one launch; the oracle recomputes a sample (random blocks of ids and the
@@ -13,17 +14,19 @@ and its activations rounded to bf16 as the tensor cores take them.
 The bar is the one of the constant-bias steppers: step counts identical except
 near-ties and network partings, at most 1% of the sample; on identical step
 counts |ln w_gpu - ln w_oracle| <= 1e-4 max(1, |ln w|) on every trajectory
-that no network parting explains. A network parting: the two sides round an
-activation to bf16 in different directions (their pre-activations differ by
-FP32 against FP64 accumulation, ~1e-7 relative, and a value that close to a
-rounding boundary goes either way), so alpha of one segment differs by a bf16
-step of one activation instead of ~1e-6. It is shown per trajectory: the GPU
-network evaluated at the oracle's own segment states (fpt_mlp_eval, the
-stepper's device code) differs from the oracle's alpha by more than the
+that no network parting explains. A network parting: the two sides round a
+network input or activation to bf16 in different directions (their values
+differ by FP32 against FP64 arithmetic, ~1e-7 relative, and a value that close
+to a rounding boundary goes either way), so alpha of one segment differs by a
+bf16 step instead of ~1e-6. It is shown per trajectory: the GPU's alpha along
+its own path (fpt_run_records) differs from the oracle's by more than the
 forward tolerance at some segment, and the ln w difference that those alpha
 differences predict, sum_s dalpha_s d ln w/d alpha_s with d ln w/d alpha_s =
 -(alpha_s m_s dN + sqrt(dN) sum of xi over s) from the oracle's segment
-records, accounts for the observed one within the bar.
+records, accounts for the observed one within the bar. The log-field input is
+floored (ln max(x, 2^-14 x_in)): without the floor, the field's FP32 rounding
+(~1e-13) made ln x differ by up to 1e-3 a step before passage, and a few
+partings per path moved ln w by ~5e-3.
 """
 import json
 import math
@@ -80,7 +83,7 @@ def test_learned_stepper_matches_oracle_per_trajectory(torch, setup):
     with fpt.fpt_init_model([m]) as ctx:
         fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
         prop = TR.new_proposal(ctx, v, shift=shift, scale=scale, segment=seg, alpha_max=amax,
-                               flags=fpt.FPT_MLP_LOG_X)
+                               flags=fpt.FPT_MLP_LOG_X, x_floor=fx["x_floor"])
         out = dict(nsteps=torch.zeros(n, dtype=torch.int32, device="cuda"),
                    logw=torch.zeros(n, dtype=torch.float64, device="cuda"),
                    status=torch.zeros(n, dtype=torch.uint8, device="cuda"))
@@ -94,7 +97,7 @@ def test_learned_stepper_matches_oracle_per_trajectory(torch, setup):
         del out
 
         mlp = OS.MLPBias(p, segment=seg, in_shift=shift, in_scale=scale, alpha_max=amax, round_bf16=True,
-                         log_x=True)
+                         log_x=True, x_floor=fx["x_floor"])
         rows = [OS.run(m, res, tab, seed=seed, run_id=0, n=w, traj0=s, mlp=mlp) for s, w in blocks]
         o = {k: np.concatenate([getattr(r, k) for r in rows])
              for k in ("nsteps", "logw", "status", "phi_final", "xmin_pre")}
@@ -113,9 +116,11 @@ def test_learned_stepper_matches_oracle_per_trajectory(torch, setup):
             tid = int(ids[j])
             tr = OS.run_segments(m, res, tab, mlp, seed=seed, run_id=0, traj=tid, cap=1 << 13)
             assert tr["nsteps"] == o["nsteps"][j] and tr["logw"] == pytest.approx(o["logw"][j], rel=1e-12)
-            s_norm = ((tr["state"] - np.asarray(shift)) * np.asarray(scale)).astype(np.float32)
-            a_gpu, _ = fpt.fpt_mlp_eval(ctx, prop.blob, s_norm, tr["tan_theta"].astype(np.float32), amax)
-            d = np.asarray(a_gpu, np.float64) - tr["alpha"]
+            # the GPU's own alpha along its path (segment records of the same trajectory)
+            rec = fpt.fpt_run_records(ctx, prop.desc(0, 1, seed=seed, run_id=0, traj_offset=tid), cap=1 << 13)
+            k = min(len(rec["raw"]), len(tr["alpha"]))
+            d = np.zeros(len(tr["alpha"]))
+            d[:k] = np.clip(rec["raw"][:k], -amax, amax) - tr["alpha"][:k]
             part = np.abs(d) > FWD_TOL * np.maximum(1.0, np.abs(tr["alpha"]))
             k = len(tr["alpha"])
             msteps = np.full(k, float(seg))
@@ -153,7 +158,8 @@ def test_network_forward_matches_oracle_on_trained_weights(torch, setup):
     fx, p, m, res, tab = setup
     shift, scale = tuple(fx["shift"]), tuple(fx["scale"])
     seg, amax = int(fx["segment"]), float(fx["alpha_max"])
-    mlp = OS.MLPBias(p, segment=seg, in_shift=shift, in_scale=scale, alpha_max=amax, round_bf16=True, log_x=True)
+    mlp = OS.MLPBias(p, segment=seg, in_shift=shift, in_scale=scale, alpha_max=amax, round_bf16=True, log_x=True,
+                     x_floor=fx["x_floor"])
     S_, A_, T_ = [], [], []
     for j in range(24):
         tr = OS.run_segments(m, res, tab, mlp, seed=77, run_id=0, traj=j, cap=1 << 13)
@@ -187,14 +193,14 @@ def test_learned_segments_match_oracle(torch, setup):
     seg, amax = int(fx["segment"]), float(fx["alpha_max"])
     v = fpt.canonical_params(p)
     mlp = OS.MLPBias(p, segment=seg, in_shift=tuple(shift), in_scale=tuple(scale), alpha_max=amax,
-                     round_bf16=True, log_x=True)
+                     round_bf16=True, log_x=True, x_floor=fx["x_floor"])
     ids = [232901, 232907, 232908, 232918, 232933, 944513, 5, 77]
     sdN = math.sqrt(m.dN)
     rows = []
     with fpt.fpt_init_model([m]) as ctx:
         fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_BESSEL, W.USR_TABLE.n_points, W.USR_TABLE.sigma)
         prop = TR.new_proposal(ctx, v, shift=tuple(shift), scale=tuple(scale), segment=seg, alpha_max=amax,
-                               flags=fpt.FPT_MLP_LOG_X)
+                               flags=fpt.FPT_MLP_LOG_X, x_floor=fx["x_floor"])
         for tid in ids:
             d = prop.desc(0, 1, seed=4, run_id=0, traj_offset=tid)
             st, g = gpu_run(ctx, [d], [1])
