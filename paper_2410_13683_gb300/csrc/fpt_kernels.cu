@@ -567,11 +567,13 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
             // it -- a step moves the field by at most s_max (|xi| + |alpha| sqrt(dN))
             // + |pi| dN with |xi| <= 5.77 (the largest Box-Muller radius of a
             // 23-bit uniform), taken here with a factor 2 to spare -- and four
-            // steps stay under the cap, the four steps run without the per-step
+            // steps stay below the cap (the step that reaches the cap is taken on
+            // the guarded path, which marks the trajectory capped there), the four
+            // steps run without the per-step
             // passage test and branch. The arithmetic of a step is the same on
             // both paths, so results do not depend on which one ran.
             const bool fast = SMEM &&
-                __all_sync(FULL, active && !done && L.n + 4 <= P.m0.max_steps &&
+                __all_sync(FULL, active && !done && L.n + 4 < P.m0.max_steps &&
                                      __fsub_rn(L.x, L.x_c) >
                                          8.0f * fmaf(P.m0.s_max, 5.8f + fabsf(L.cb), fabsf(L.p) * P.m0.dN));
             if (fast) {
