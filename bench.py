@@ -485,35 +485,52 @@ def batched_bias_leg(fpt, torch, shard, m, stream, seed, rank, N_tail, sm_count,
 
 
 def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max, autotune=True, n=1 << 11,
-                     pts=256, A_fallback=4.0):
+                     pts=256, A_fallback=4.0, rounds=20):
     """The batched sweep over 64 piecewise-linear models (a- log-uniform in
     [1e-7, 1e-4], phi* in [0.9, 1.1], V0 log-uniform in [1e-11, 1e-9]), each
-    with its learned proposal and its constant-bias fallback A = 4: 128 runs
-    of uneven lengths (step cap 2^23) in one persistent launch, tables read
-    through L1, the networks evaluated per run, block shape and refill
-    interval from the autotuner, replayed as a captured CUDA graph. Each
-    model's proposal is the network trained on the sudden-transition model,
-    applied in that model's own input normalisation (ln x / x_in, pi / |pi_in|):
-    one network per run in the launch, not a network trained per model."""
+    with its own learned proposal and its constant-bias fallback A = 4: 128
+    runs of uneven lengths (step cap 2^23) in one persistent launch, tables read
+    through L1, one network per run, block shape and refill interval from the
+    autotuner, replayed as a captured CUDA graph.
+
+    Proposals: the network trained on the sudden-transition model, in each
+    model's own normalisation (ln x / x_in, pi / |pi_in|), then trained further
+    per model -- all 64 networks in one generation launch per round
+    (fpt_mlp_train_batch) -- towards e^{lambda min(N, N_cut)} with N_cut = 30 <N>
+    of the model's direct paths (the sudden-transition model's N_12 is 30 <N>),
+    at most 200 e-folds (which keeps a round's segment records in the buffer). Per model: tail ESS over {N >= N_cut} of the learned
+    run against its fallback run in the same launch."""
     models = W.batch_models(64)
+    K = len(models)
     ctx = fpt.fpt_init_model(models, device=torch.cuda.current_device())
     t0 = time.perf_counter()
-    for i in range(len(models)):
+    for i in range(K):
         fpt.fpt_noise_table(ctx, i, fpt.FPT_TABLE_BESSEL, pts, 1.0)
     table_s = time.perf_counter() - t0
-    blob = TR.new_proposal(ctx, prop.params.detach().cpu().numpy(), shift=prop.shift, scale=prop.scale,
-                           segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags)
-    props = []
-    for i in range(len(models)):
-        info = fpt.fpt_model_get_info(ctx, i)
-        x_in = info["phi_in"] - info["phi_end"]
-        props.append(TR.Proposal(blob.params, blob.blob, (math.log(x_in), 0.0, 0.0),
-                                 (prop.scale[0], 1.0 / abs(info["pi_in"]), prop.scale[2]), prop.segment,
-                                 prop.alpha_max, prop.flags, x_in * X_FLOOR_REL))
+    # pilot: direct paths of every model in one launch give <N> and the tail points
+    fpt.fpt_run(ctx, [fpt.run_desc(i, n, seed=seed + 69, run_id=i) for i in range(K)], stream=stream)
+    cuts = []
+    for i in range(K):
+        h = fpt.fpt_histogram(ctx, i, 0.0, 1e4, 64, stream=stream)
+        meanN = h["N_mean"] if h["n_passed"] > 0 else models[i].max_steps * models[i].dN
+        cuts.append(float(min(30.0 * meanN, 200.0, 0.5 * models[i].max_steps * models[i].dN)))
+    infos = [fpt.fpt_model_get_info(ctx, i) for i in range(K)]
+    x_ins = [inf["phi_in"] - inf["phi_end"] for inf in infos]
+    v = prop.params.detach().cpu().numpy()
+    props, P, B = TR.new_proposals(ctx, [v] * K, [(math.log(x), 0.0, 0.0) for x in x_ins],
+                                   [(prop.scale[0], 1.0 / abs(inf["pi_in"]), prop.scale[2]) for inf in infos],
+                                   segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags,
+                                   x_floors=[x * X_FLOOR_REL for x in x_ins])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    TR.train_batch(ctx, props, P, B, list(range(K)), rounds=rounds, n_traj=n // 2, seed=seed + 71, lam=0.25,
+                   N_cuts=cuts, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
 
     def runs(k):
         out = []
-        for i in range(len(models)):
+        for i in range(K):
             out.append(props[i].desc(i, n, seed=seed + 70, run_id=2 * (64 * k + i), traj_offset=rank * n))
             out.append(fpt.run_desc(i, n, seed=seed + 70, run_id=2 * (64 * k + i) + 1, A=A_fallback,
                                     traj_offset=rank * n))
@@ -528,28 +545,38 @@ def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max,
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    steps, capped, passed = 0.0, 0, 0
-    lengths = []
-    for r in range(2 * len(models)):
-        h = fpt.fpt_histogram(ctx, r, 0.0, 1e4, 64, stream=stream)
-        m = models[r // 2]
-        steps += passed_steps(h, m.dN) + h["n_capped"] * float(m.max_steps)
-        capped += int(h["n_capped"])
-        passed += int(h["n_passed"])
-        if h["n_passed"] > 0:
-            lengths.append(h["N_mean"])
+    steps, capped = 0.0, 0
+    gains, ess_l, ess_f = [], 0.0, 0.0
+    for i in range(K):
+        m = models[i]
+        e = []
+        for r in (2 * i, 2 * i + 1):
+            h = fpt.fpt_histogram(ctx, r, 0.0, 1e4, 64, N_tail=cuts[i], stream=stream)
+            steps += passed_steps(h, m.dN) + h["n_capped"] * float(m.max_steps)
+            capped += int(h["n_capped"])
+            e.append(float(h["ess_tail"]))
+        ess_l += e[0]
+        ess_f += e[1]
+        if e[1] > 0:
+            gains.append(e[0] / e[1])
     fpt.fpt_sync(ctx)
     ctx.close()
     rl = roofline(steps, ms, sm_count, sm_max, None, INSTR_PER_STEP)
     rl["kernel"] = "em_kernel<weighted, tables via L1, MLP, one network per run>"
-    return {"models": len(models), "runs": 2 * len(models), "n_traj_per_run": n, "table_points": pts,
+    return {"models": K, "runs": 2 * K, "n_traj_per_run": n, "table_points": pts,
             "table_build_s": round(table_s, 2), "launch": launch, "launch_ms": ms,
-            "traj_per_s": 2 * len(models) * n / (ms * 1e-3), "em_steps_per_s": steps / (ms * 1e-3),
-            "roofline": rl, "censored_fraction": capped / float(2 * len(models) * n),
-            "mean_N_passed_min_max": [min(lengths), max(lengths)] if lengths else None,
-            "proposal": "sudden-transition network in each model's normalisation; fallback A = %g" % A_fallback,
-            "note": "2^11 trajectories per run instead of 2^20: the A = 4 fallback sends every path to the 2^23-step "
-                    "cap (at 2^20 per run that alone is 5.6e14 EM steps)"}
+            "traj_per_s": 2 * K * n / (ms * 1e-3), "em_steps_per_s": steps / (ms * 1e-3),
+            "roofline": rl, "censored_fraction": capped / float(2 * K * n),
+            "train": {"rounds": rounds, "seconds": round(train_s, 2), "traj_per_model_per_round": n // 2,
+                      "launches_per_round": 1,
+                      "N_cut": "30 <N> of the model's direct paths, at most 200 e-folds and half the cap"},
+            "tail_ess_learned_total": ess_l, "tail_ess_fallback_total": ess_f,
+            "tail_ess_gain_median": float(np.median(gains)) if gains else None,
+            "models_with_fallback_tail": len(gains),
+            "proposal": "per-model networks (warm start: the sudden-transition network in the model's "
+                        "normalisation); fallback A = %g" % A_fallback,
+            "note": "2^11 trajectories per run instead of 2^20: the A = 4 fallback sends most paths to the "
+                    "2^23-step cap (at 2^20 per run that alone is 5.6e14 EM steps)"}
 
 
 PEAK_SIGMA = 0.05

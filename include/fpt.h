@@ -469,6 +469,23 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
                                fpt_train_stats *stats, void *cuda_stream);
 
 /*
+ * One training round of n_runs proposals at once, each run (an FPT_BIAS_MLP run
+ * on any model, 1-D phi-indexed table) with its own network: run k must use
+ * blob k (blobs + k FPT_MLP_BLOB_BYTES, device) and its parameters and Adam
+ * moments are params / adam_m / adam_v + k FPT_MLP_PARAMS (device floats). All
+ * runs are generated in one launch with segment records (the runs share
+ * mlp_segment); each run's records, in (trajectory, segment) order, give the
+ * gradient of its own log-variance loss Var[ln w + lambda min(N, N_cut[k])]
+ * over its own paths (as fpt_mlp_train_round with one chunk), then one Adam step
+ * and a re-pack per network. stats (n_runs entries, nullable): loss, mean_Y,
+ * mean_N, n_traj, n_records, n_capped per run (grad_norm NaN). FPT_E_NOMEM if
+ * the records exceed 2^29. Blocks until done.
+ */
+fpt_status fpt_mlp_train_batch(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, double lambda,
+                               const double *N_cut, const fpt_adam *adam, float *params, float *adam_m,
+                               float *adam_v, void *blobs, fpt_train_stats *stats, void *cuda_stream);
+
+/*
  * The held-alpha segments of one learned-proposal run (Sec. 5's open bias made
  * concrete: what the proposal did along each path), for analysis and tests:
  * the run (one FPT_BIAS_MLP run, 1-D table) is generated in record mode, the

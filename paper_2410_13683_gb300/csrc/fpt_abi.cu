@@ -898,10 +898,10 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     // an MLP run cannot also carry a run on a time-indexed (noise-window) table
     if (mlp_run >= 0 && nidx)
         return fail(ctx, FPT_E_INVALID, "a call with a learned-proposal run needs phi-indexed tables for all its runs");
-    if (mnet && (rank2 == 1 || bump == 1 || ctx->record_mode))
+    if (mnet && (rank2 == 1 || bump == 1))
         return fail(ctx, FPT_E_INVALID,
                     "MLP runs with different networks need 1-D noise tables and the piecewise-linear or "
-                    "exponential potential (and are not recorded for training)");
+                    "exponential potential");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
     fpt_status st = ensure_units(ctx, std::max<long long>(total, 1));
@@ -1528,6 +1528,131 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
         stats->n_records = n_rec_total;
         stats->n_capped = n_capped;
         stats->grad_norm = std::sqrt(gn2);
+    }
+    return FPT_OK;
+}
+
+fpt_status fpt_mlp_train_batch(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, double lambda,
+                               const double *N_cut, const fpt_adam *adam, float *params, float *adam_m,
+                               float *adam_v, void *blobs, fpt_train_stats *stats, void *cuda_stream)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (!runs || n_runs < 1 || n_runs > kMaxRuns || !N_cut || !adam || !params || !adam_m || !adam_v || !blobs)
+        return fail(ctx, FPT_E_INVALID, "null argument or n_runs out of [1, 128]");
+    if (!(adam->lr > 0) || adam->step < 1) return fail(ctx, FPT_E_INVALID, "bad Adam settings");
+    if (!std::isfinite(lambda)) return fail(ctx, FPT_E_INVALID, "bad lambda");
+    if (!is_device_ptr(params) || !is_device_ptr(adam_m) || !is_device_ptr(adam_v) || !is_device_ptr(blobs))
+        return fail(ctx, FPT_E_INVALID, "params, Adam moments and blobs must be device buffers");
+    long long total = 0;
+    std::vector<long long> begin(n_runs + 1, 0);
+    for (int k = 0; k < n_runs; ++k) {
+        const fpt_run_desc &d = runs[k];
+        if (d.bias_kind != FPT_BIAS_MLP ||
+            d.mlp != static_cast<const char *>(blobs) + (size_t)k * kMlpBlobBytes)
+            return fail(ctx, FPT_E_INVALID, "run k must be an MLP run on blob k (blobs + k FPT_MLP_BLOB_BYTES)");
+        if (d.model < 0 || d.model >= (int)ctx->models.size()) return fail(ctx, FPT_E_INVALID, "run model out of range");
+        if (!(N_cut[k] > 0)) return fail(ctx, FPT_E_INVALID, "N_cut must be positive");
+        if (d.n_traj < 2) return fail(ctx, FPT_E_INVALID, "every run needs n_traj >= 2");
+        begin[k] = total;
+        total += d.n_traj;
+    }
+    begin[n_runs] = total;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    // record buffer: every run's paths' segments
+    long long want = 0;
+    for (int k = 0; k < n_runs; ++k)
+        want += runs[k].n_traj * (ctx->models[runs[k].model].max_steps / std::max(4, runs[k].mlp_segment) + 2);
+    want = std::min<long long>(want, 1LL << 29);
+    if (want > ctx->rec_cap) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(ctx->d_records);
+        ctx->d_records = nullptr;
+        ctx->rec_cap = 0;
+        clear_graphs(ctx);
+        CK(cudaMalloc(&ctx->d_records, sizeof(float) * 8 * want));
+        ctx->rec_cap = want;
+    }
+    const size_t acc_doubles = mlp_coef_scratch_doubles();
+    if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
+    if (!ctx->d_rec_err) CK(cudaMalloc(&ctx->d_rec_err, 64));
+    fpt_status st;
+    if ((st = ensure_dev(ctx, ctx->d_coef, ctx->coef_cap, total)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_Y, ctx->y_cap, total)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_perm, ctx->perm_cap, ctx->rec_cap)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_cnt, ctx->cnt_cap, total)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_off, ctx->off_cap, total)) != FPT_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, (long long)n_runs * kMlpParams)) != FPT_OK) return st;
+    if ((st = ensure_gpart(ctx)) != FPT_OK) return st;
+    double *d_accs = nullptr;
+    CK(cudaMalloc(&d_accs, sizeof(double) * acc_doubles * n_runs));
+    struct Free { double *p; ~Free() { cudaFree(p); } } free_accs{d_accs};
+
+    // one launch generates every run's paths with segment records
+    ctx->record_mode = true;
+    st = fpt_run(ctx, runs, n_runs, nullptr, s);
+    ctx->record_mode = false;
+    if (st != FPT_OK) return st;
+    st = fpt_sync(ctx);
+    if (st == FPT_E_TIMEOUT) return st;
+    if (ctx->h_flags[3]) return fail(ctx, FPT_E_NOMEM, "segment records exceed the record buffer; use fewer paths");
+    unsigned long long n_rec = 0;
+    CK(cudaMemcpy(&n_rec, ctx->d_rec_cursor, sizeof(n_rec), cudaMemcpyDeviceToHost));
+    // records in (trajectory, segment) order: run k's records are one contiguous range
+    CK(rec_order_launch(ctx->d_records, (long long)n_rec, total, runs[0].mlp_segment, ctx->d_cnt, ctx->d_off,
+                        ctx->d_perm, ctx->d_rec_err, s));
+    std::vector<long long> off(total);
+    std::vector<int32_t> nsteps(total);
+    std::vector<uint8_t> status(total);
+    CK(cudaMemcpyAsync(off.data(), ctx->d_off, sizeof(long long) * total, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nsteps.data(), ctx->d_nsteps, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(status.data(), ctx->d_status, total, cudaMemcpyDeviceToHost, s));
+    int rec_err = 0;
+    CK(cudaMemcpyAsync(&rec_err, ctx->d_rec_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (rec_err) return fail(ctx, FPT_E_STATE, "segment records out of order (code " + std::to_string(rec_err) + ")");
+    float *d_grads = ctx->d_tmp;
+    CK(cudaMemsetAsync(d_grads, 0, sizeof(float) * (size_t)n_runs * kMlpParams, s));
+    for (int k = 0; k < n_runs; ++k) {
+        const fpt_run_desc &d = runs[k];
+        const fpt_model &m = ctx->models[d.model];
+        const long long b = begin[k], n = d.n_traj;
+        const long long r0 = off[b], r1 = (k + 1 < n_runs) ? off[begin[k + 1]] : (long long)n_rec;
+        // coefficients of run k's paths at their launch units (the backward indexes coef by unit)
+        CK(mlp_coef_launch(ctx->d_nsteps + b, ctx->d_logw + b, n, m.dN, lambda, N_cut[k], 2.0 / (double)n,
+                           ctx->d_Y + b, d_accs + (size_t)k * acc_doubles, ctx->d_coef + b, s));
+        CK(mlp_bwd_launch(params + (size_t)k * kMlpParams, ctx->d_records, r1 - r0, ctx->d_coef, (float)m.dN,
+                          d.alpha_max, nullptr, d_grads + (size_t)k * kMlpParams, ctx->sm_count, s,
+                          ctx->d_perm + r0, ctx->d_gpart, 0));
+        CK(mlp_adam_launch(params + (size_t)k * kMlpParams, d_grads + (size_t)k * kMlpParams,
+                           adam_m + (size_t)k * kMlpParams, adam_v + (size_t)k * kMlpParams, kMlpParams, adam->lr,
+                           adam->beta1, adam->beta2, adam->eps, adam->step, adam->clip, s));
+        CK(mlp_pack_launch(params + (size_t)k * kMlpParams, static_cast<char *>(blobs) + (size_t)k * kMlpBlobBytes, s));
+        if (stats) {
+            stats[k].n_traj = n;
+            stats[k].n_records = r1 - r0;
+        }
+    }
+    std::vector<double> accs(acc_doubles * n_runs);
+    CK(cudaMemcpyAsync(accs.data(), d_accs, sizeof(double) * accs.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        for (int k = 0; k < n_runs; ++k) {
+            const long long b = begin[k], n = runs[k].n_traj;
+            const double dN = ctx->models[runs[k].model].dN;
+            const double mY = accs[k * acc_doubles] / (double)n;
+            stats[k].loss = accs[k * acc_doubles + 1] / (double)n - mY * mY;
+            stats[k].mean_Y = mY;
+            double sN = 0.0;
+            long long passed = 0, capped = 0;
+            for (long long i = b; i < b + n; ++i) {
+                if (status[i] == FPT_TRAJ_PASSED) { sN += nsteps[i] * dN; ++passed; }
+                else if (status[i] == FPT_TRAJ_CAPPED) ++capped;
+            }
+            stats[k].mean_N = passed ? sN / (double)passed : NAN;
+            stats[k].n_capped = capped;
+            stats[k].grad_norm = NAN;
+        }
     }
     return FPT_OK;
 }

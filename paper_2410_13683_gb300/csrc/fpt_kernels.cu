@@ -337,8 +337,8 @@ __device__ __forceinline__ void mlp_segment_start(Lane &L, bool live, SegRec &sg
 // segment length): the warp evaluates the network of each run among its live
 // lanes in turn -- runs are contiguous in unit order, so a warp mostly holds
 // one run -- reading that run's packed weights through L1.
-template <bool SMEM>
-__device__ __forceinline__ void mlp_segment_start_multi(Lane &L, bool live, const float4 *tab,
+template <bool SMEM, bool REC>
+__device__ __forceinline__ void mlp_segment_start_multi(Lane &L, bool live, SegRec &sg, const float4 *tab,
                                                         const RunDev *runs, const ModelDev &M0)
 {
     const unsigned FULL = 0xffffffffu;
@@ -370,6 +370,12 @@ __device__ __forceinline__ void mlp_segment_start_multi(Lane &L, bool live, cons
             const float al = mlp_alpha_of(o1, o2, tan_t, pr.alpha_max, raw);
             L.cb = al * sqrt_dN;
             L.half_cb2 = 0.5f * al * al * dN;
+            if (REC) {
+                sg.in0 = in0; sg.in1 = in1; sg.in2 = in2; sg.tan_t = tan_t; sg.raw = raw;
+                sg.sum_xi = 0.0f;
+                sg.n0 = L.n;
+                sg.open = true;
+            }
         }
     }
 }
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
 
     for (;;) {
         if (MLP && __any_sync(FULL, active && L.mlp)) {
-            if (MNET) mlp_segment_start_multi<SMEM>(L, active && L.mlp, tab, P.runs, P.m0);
+            if (MNET) mlp_segment_start_multi<SMEM, REC>(L, active && L.mlp, sg, tab, P.runs, P.m0);
             else mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun, P.m0);
         }
 
@@ -773,9 +779,12 @@ static const void *em_fn_t(EmVariant v)
 
 static const void *em_fn(EmVariant v)
 {
-    if (v.mnet)   // one network per run: 1-D, phi-indexed, no records
+    if (v.mnet) {   // one network per run: 1-D, phi-indexed tables
+        if (v.rec) return v.smem ? (const void *)em_kernel<true, true, true, true, false, false, true>
+                                 : (const void *)em_kernel<true, false, true, true, false, false, true>;
         return v.smem ? (const void *)em_kernel<true, true, true, false, false, false, true>
                       : (const void *)em_kernel<true, false, true, false, false, false, true>;
+    }
     if (v.dtab) return em_fn_t<true>(v);
     if (v.nidx && !v.rank2 && !v.mlp) {
         if (v.weighted) return v.smem ? (const void *)em_kernel<true, true, false, false, true, false>

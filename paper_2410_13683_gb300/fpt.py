@@ -148,6 +148,9 @@ _SIGNATURES = {
     "fpt_mlp_train_round": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_double,
                                       C.c_double, C.POINTER(fpt_adam), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(fpt_train_stats), C.c_void_p]),
+    "fpt_mlp_train_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                                      C.POINTER(fpt_adam), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
     "fpt_run_records": (C.c_int, [C.c_void_p, C.POINTER(fpt_run_desc), C.c_int64, C.c_void_p,
                                   C.POINTER(C.c_int64), C.c_void_p]),
     "fpt_histogram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
@@ -536,6 +539,22 @@ def fpt_mlp_train_round(ctx: Context, run: fpt_run_desc, chunk: int, lam: float,
                                       _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(blob), C.byref(st),
                                       _stream(stream)), ctx.handle)
     return {k: getattr(st, k) for k, _ in fpt_train_stats._fields_}
+
+
+def fpt_mlp_train_batch(ctx: Context, runs: Sequence[fpt_run_desc], lam: float, N_cut, adam: dict, params,
+                        adam_m, adam_v, blobs, stream=None) -> list:
+    """One round for len(runs) proposals at once (run k on blob k, params row k)."""
+    arr = (fpt_run_desc * len(runs))(*runs)
+    cut = np.ascontiguousarray(N_cut, dtype=np.float64)
+    if len(cut) != len(runs):
+        raise ValueError("one N_cut per run")
+    a = fpt_adam(lr=adam["lr"], beta1=adam.get("beta1", 0.9), beta2=adam.get("beta2", 0.999),
+                 eps=adam.get("eps", 1e-8), clip=adam.get("clip", 0.0), step=adam["step"])
+    st = (fpt_train_stats * len(runs))()
+    _check(load().fpt_mlp_train_batch(ctx.handle, C.cast(arr, C.c_void_p), len(runs), lam, _ptr(cut), C.byref(a),
+                                      _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(blobs), C.cast(st, C.c_void_p),
+                                      _stream(stream)), ctx.handle)
+    return [{k: getattr(x, k) for k, _ in fpt_train_stats._fields_} for x in st]
 
 
 def canonical_params(p: dict) -> np.ndarray:

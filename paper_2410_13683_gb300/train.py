@@ -139,3 +139,57 @@ def train_select(ctx, prop: Proposal, model: int, rounds: int, checkpoints, val_
         if prop.params.is_cuda:
             torch.cuda.synchronize()
     return prop
+
+
+def new_proposals(ctx, init_params, shifts, scales, segment: int = 64, alpha_max: float = 4.0, flags: int = 0,
+                  x_floors=None):
+    """len(init_params) proposals whose parameters and packed blobs are the
+    rows of two shared device tensors, as fpt_mlp_train_batch expects."""
+    import torch
+    n = len(init_params)
+    P = torch.tensor(np.stack([np.asarray(v, np.float32) for v in init_params]), device="cuda")
+    B = torch.zeros((n, fpt.FPT_MLP_BLOB_BYTES), dtype=torch.uint8, device="cuda")
+    for k in range(n):
+        fpt.fpt_mlp_pack(ctx, P[k], B[k])
+    torch.cuda.synchronize()
+    fl = list(x_floors) if x_floors is not None else [0.0] * n
+    props = [Proposal(P[k], B[k], tuple(float(v) for v in shifts[k]), tuple(float(v) for v in scales[k]), segment,
+                      alpha_max, flags, float(fl[k])) for k in range(n)]
+    return props, P, B
+
+
+def train_batch(ctx, props, P, B, models, rounds: int, n_traj: int, seed: int, lam: float, N_cuts, lr=3e-3,
+                clip: float = 0.0, first_round: int = 0, log: Optional[Callable[[list], None]] = None):
+    """`rounds` Adam steps of every proposal at once (fpt_mlp_train_batch):
+    proposal k trains on model models[k], n_traj fresh paths per round
+    (Philox run id = round * len(props) + k). N_cuts: one N_cut per proposal,
+    or a function of the round giving the list."""
+    import torch
+    if not hasattr(P, "_adam"):
+        P._adam = (torch.zeros_like(P), torch.zeros_like(P))
+    m, v = P._adam
+    hist = []
+    for r in range(first_round, first_round + rounds):
+        runs = [props[k].desc(models[k], n_traj, seed=seed, run_id=r * len(props) + k) for k in range(len(props))]
+        cuts = N_cuts(r) if callable(N_cuts) else N_cuts
+        lr_r = lr(r) if callable(lr) else lr
+        nn = n_traj
+        while True:
+            try:
+                st = fpt.fpt_mlp_train_batch(ctx, runs, lam, cuts, dict(lr=lr_r, step=r + 1, clip=clip), P, m, v, B)
+                break
+            except fpt.FptError as e:
+                # more segment records than the buffer holds: the round left the
+                # parameters untouched, so it is redone on half the paths
+                if e.status != fpt.FPT_E_NOMEM or nn <= 64:
+                    raise
+                nn //= 2
+                runs = [props[k].desc(models[k], nn, seed=seed, run_id=r * len(props) + k)
+                        for k in range(len(props))]
+        for k, s in enumerate(st):
+            s["round"] = r
+            props[k].history.append(s)
+        hist.append(st)
+        if log:
+            log(st)
+    return hist

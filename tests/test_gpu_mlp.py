@@ -237,3 +237,37 @@ def test_training_is_deterministic(torch):
     assert np.array_equal(p1.view(np.uint32), p2.view(np.uint32))
     assert l1 == l2 and g1 == g2
     assert not np.array_equal(p1, v0)
+
+
+def test_batch_training_equals_single_runs(torch):
+    """fpt_mlp_train_batch trains several networks, on different models, in
+    one generation launch; each network's round equals fpt_mlp_train_round on
+    its run alone (one chunk), bit for bit: the same paths, the run's records
+    in the same order, the same coefficients and the same tiles."""
+    from dataclasses import replace
+    m0 = W.BM.model
+    m1 = replace(m0, mu=0.012, pi_in=-0.012)
+    S, T = np.full(16, W.BM_S), np.zeros(16)
+    inits = [fpt.canonical_params(W.mlp_init(40 + k, out_scale=0.2)) for k in range(3)]
+    shifts = [(0.025, -0.01, 3.0)] * 3
+    scales = [(40.0, 100.0, 0.3), (30.0, 80.0, 0.3), (40.0, 100.0, 0.2)]
+    models = [0, 1, 0]
+    n = 3000
+    with fpt.fpt_init_model([m0, m1]) as ctx:
+        for i in range(2):
+            fpt.fpt_noise_table(ctx, i, fpt.FPT_TABLE_USER, 16, 1.0, -0.1, 0.2, S, T)
+        props, P, B = TR.new_proposals(ctx, inits, shifts, scales, segment=64, alpha_max=4.0)
+        hist = TR.train_batch(ctx, props, P, B, models, rounds=2, n_traj=n, seed=23, lam=9.5,
+                              N_cuts=[1e9, 1e9, 1e9], lr=1e-2)
+        got = P.cpu().numpy().copy()
+        for k in range(3):
+            alone = TR.new_proposal(ctx, inits[k], shift=shifts[k], scale=scales[k], segment=64, alpha_max=4.0)
+            m_, v_ = torch.zeros_like(alone.params), torch.zeros_like(alone.params)
+            for r in range(2):
+                run = alone.desc(models[k], n, seed=23, run_id=r * 3 + k)
+                st = fpt.fpt_mlp_train_round(ctx, run, n, 9.5, 1e9, dict(lr=1e-2, step=r + 1), alone.params, m_, v_,
+                                             alone.blob)
+                assert st["n_records"] == hist[r][k]["n_records"]
+                assert st["loss"] == pytest.approx(hist[r][k]["loss"], rel=1e-12)
+            assert np.array_equal(alone.params.cpu().numpy().view(np.uint32), got[k].view(np.uint32)), k
+    assert not np.array_equal(got[0], got[2])
