@@ -546,7 +546,7 @@ def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max,
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     steps, capped = 0.0, 0
-    gains, ess_l, ess_f = [], 0.0, 0.0
+    gains, ess_l, ess_f, with_l = [], 0.0, 0.0, 0
     for i in range(K):
         m = models[i]
         e = []
@@ -557,6 +557,7 @@ def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max,
             e.append(float(h["ess_tail"]))
         ess_l += e[0]
         ess_f += e[1]
+        with_l += int(e[0] > 0)
         if e[1] > 0:
             gains.append(e[0] / e[1])
     fpt.fpt_sync(ctx)
@@ -571,8 +572,8 @@ def model_family_leg(fpt, torch, TR, prop, stream, seed, rank, sm_count, sm_max,
                       "launches_per_round": 1,
                       "N_cut": "30 <N> of the model's direct paths, at most 200 e-folds and half the cap"},
             "tail_ess_learned_total": ess_l, "tail_ess_fallback_total": ess_f,
-            "tail_ess_gain_median": float(np.median(gains)) if gains else None,
-            "models_with_fallback_tail": len(gains),
+            "models_with_learned_tail": with_l, "models_with_fallback_tail": len(gains),
+            "tail_ess_gain_median_where_fallback_reaches": float(np.median(gains)) if gains else None,
             "proposal": "per-model networks (warm start: the sudden-transition network in the model's "
                         "normalisation); fallback A = %g" % A_fallback,
             "note": "2^11 trajectories per run instead of 2^20: the A = 4 fallback sends most paths to the "

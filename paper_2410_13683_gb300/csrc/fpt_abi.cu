@@ -681,8 +681,10 @@ static fpt_status upload_tables(fpt_ctx *ctx)
             }
             const double sq = std::sqrt(m.dN);
             d.rank2 = t.rank2 ? 1 : 0;
+            // bound of a step's field noise per unit normal: S_phiphi (1-D), S_phiphi + |S_phipi| (2-D)
             double smax = 0.0;
-            for (int j = 0; j < t.M; ++j) smax = std::max(smax, std::fabs(t.S[j]) * sq);
+            for (int j = 0; j < t.M; ++j)
+                smax = std::max(smax, (std::fabs(t.S[j]) + (t.rank2 ? std::fabs(t.T[j]) : 0.0)) * sq);
             d.s_max = (float)(smax * (1.0 + 1e-6));
             if (t.rank2) {
                 // (S_phiphi, S_phipi, S_pipi, 0) sqrt(dN); entry M repeats entry M - 1

@@ -14,7 +14,7 @@ from oracle import tables as OT
 from paper_2410_13683_gb300 import fpt
 from paper_2410_13683_gb300 import train as TR
 
-from gpu_common import require_gpu
+from gpu_common import gpu_run, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -257,17 +257,25 @@ def test_batch_training_equals_single_runs(torch):
         for i in range(2):
             fpt.fpt_noise_table(ctx, i, fpt.FPT_TABLE_USER, 16, 1.0, -0.1, 0.2, S, T)
         props, P, B = TR.new_proposals(ctx, inits, shifts, scales, segment=64, alpha_max=4.0)
-        hist = TR.train_batch(ctx, props, P, B, models, rounds=2, n_traj=n, seed=23, lam=9.5,
-                              N_cuts=[1e9, 1e9, 1e9], lr=1e-2)
-        got = P.cpu().numpy().copy()
-        for k in range(3):
-            alone = TR.new_proposal(ctx, inits[k], shift=shifts[k], scale=scales[k], segment=64, alpha_max=4.0)
-            m_, v_ = torch.zeros_like(alone.params), torch.zeros_like(alone.params)
-            for r in range(2):
-                run = alone.desc(models[k], n, seed=23, run_id=r * 3 + k)
-                st = fpt.fpt_mlp_train_round(ctx, run, n, 9.5, 1e9, dict(lr=1e-2, step=r + 1), alone.params, m_, v_,
-                                             alone.blob)
-                assert st["n_records"] == hist[r][k]["n_records"]
-                assert st["loss"] == pytest.approx(hist[r][k]["loss"], rel=1e-12)
-            assert np.array_equal(alone.params.cpu().numpy().view(np.uint32), got[k].view(np.uint32)), k
+        alones = [TR.new_proposal(ctx, inits[k], shift=shifts[k], scale=scales[k], segment=64, alpha_max=4.0)
+                  for k in range(3)]
+        moms = [(torch.zeros_like(a.params), torch.zeros_like(a.params)) for a in alones]
+        for r in range(2):
+            # the paths of each run in the batched launch equal the run alone
+            runs = [props[k].desc(models[k], n, seed=23, run_id=r * 3 + k) for k in range(3)]
+            _, together = gpu_run(ctx, runs, [n] * 3)
+            for k in range(3):
+                _, alone_out = gpu_run(ctx, [alones[k].desc(models[k], n, seed=23, run_id=r * 3 + k)], [n])
+                assert np.array_equal(alone_out[0]["nsteps"], together[k]["nsteps"]), (r, k, "paths")
+                assert np.array_equal(alone_out[0]["logw"], together[k]["logw"]), (r, k, "paths")
+            hist = TR.train_batch(ctx, props, P, B, models, rounds=1, n_traj=n, seed=23, lam=9.5,
+                                  N_cuts=[1e9, 1e9, 1e9], lr=1e-2, first_round=r)
+            got = P.cpu().numpy().copy()
+            for k in range(3):
+                run = alones[k].desc(models[k], n, seed=23, run_id=r * 3 + k)
+                st = fpt.fpt_mlp_train_round(ctx, run, n, 9.5, 1e9, dict(lr=1e-2, step=r + 1), alones[k].params,
+                                             moms[k][0], moms[k][1], alones[k].blob)
+                assert st["n_records"] == hist[0][k]["n_records"], (r, k)
+                assert st["loss"] == pytest.approx(hist[0][k]["loss"], rel=1e-12), (r, k)
+                assert np.array_equal(alones[k].params.cpu().numpy().view(np.uint32), got[k].view(np.uint32)), (r, k)
     assert not np.array_equal(got[0], got[2])
