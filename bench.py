@@ -1072,6 +1072,9 @@ def main():
                                 "sample": f"{args.cpu_traj} trajectories of the same workload with the "
                                           f"constant-bias proposal A={A_fixed} ({nsteps} Euler-Maruyama "
                                           f"steps, {dt:.1f} s)"}
+        # the same method on both sides: the GPU's constant-bias rate over the oracle's
+        if "fixed_bias" in extras and e > 0:
+            line["gpu_vs_oracle_same_proposal"] = extras["fixed_bias"]["ess_tail_per_s"] / (e / dt)
     for c in ctxs:
         fpt.fpt_sync(c)
         c.close()

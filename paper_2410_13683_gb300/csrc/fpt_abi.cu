@@ -1625,7 +1625,7 @@ fpt_status fpt_mlp_train_batch(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n
                            ctx->d_Y + b, d_accs + (size_t)k * acc_doubles, ctx->d_coef + b, s));
         CK(mlp_bwd_launch(params + (size_t)k * kMlpParams, ctx->d_records, r1 - r0, ctx->d_coef, (float)m.dN,
                           d.alpha_max, nullptr, d_grads + (size_t)k * kMlpParams, ctx->sm_count, s,
-                          ctx->d_perm + r0, ctx->d_gpart, 0));
+                          ctx->d_perm + r0, ctx->d_gpart, 0, (long long)n_rec));
         CK(mlp_adam_launch(params + (size_t)k * kMlpParams, d_grads + (size_t)k * kMlpParams,
                            adam_m + (size_t)k * kMlpParams, adam_v + (size_t)k * kMlpParams, kMlpParams, adam->lr,
                            adam->beta1, adam->beta2, adam->eps, adam->step, adam->clip, s));

@@ -161,7 +161,7 @@ cudaError_t mlp_coef_launch(const int32_t *nsteps, const double *logw, long long
                             double N_cut, double scale, double *Y, double *acc, float *coef, cudaStream_t s);
 cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_rec, const float *coef, float dN,
                            float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s,
-                           const uint32_t *perm, float *partial, int rank2 = 0);
+                           const uint32_t *perm, float *partial, int rank2 = 0, long long rec_bound = 0);
 int mlp_bwd_max_blocks(int sm_count);
 size_t mlp_coef_scratch_doubles();
 cudaError_t rec_order_launch(const float *rec, long long n_rec, long long n_units, int segment, int *cnt,

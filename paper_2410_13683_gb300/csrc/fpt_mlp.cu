@@ -323,7 +323,7 @@ __device__ __forceinline__ void st_bf16x2(__nv_bfloat16 *p, float lo, float hi)
 }
 
 __global__ void __launch_bounds__(kBwdWarps * 32)
-mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long long n_rec,
+mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long long n_rec, long long rec_bound,
                const float *__restrict__ coef, float neg_sqrt_dN, float amax,
                const float *__restrict__ dalpha_direct, const uint32_t *__restrict__ perm,
                float *__restrict__ partial, int rank2)
@@ -387,9 +387,9 @@ mlp_bwd_kernel(const float *__restrict__ P, const float *__restrict__ rec, long 
             const long long slot = tile * kBwdRows + tid;
             // records in a fixed order; a slot the ordering left unfilled (it
             // reports that as an error) reads as an empty row
-            const long long r = slot < n_rec ? (perm ? (long long)perm[slot] : slot) : n_rec;
+            const long long r = slot < n_rec ? (perm ? (long long)perm[slot] : slot) : rec_bound;
             float in0 = 0, in1 = 0, in2 = 0, tq = 0, da = 0;
-            if (r < n_rec) {
+            if (r < rec_bound) {
                 const float *q = rec + 8 * r;
                 in0 = q[0]; in1 = q[1]; in2 = q[2]; tq = q[3];
                 if (rank2) {
@@ -620,18 +620,21 @@ int mlp_bwd_max_blocks(int sm_count) { return 3 * sm_count; }
 // The gradient of a call is deterministic: records in the order perm gives
 // (nullptr: buffer order), tiles statically assigned to blocks, per-block
 // partials (partial: mlp_bwd_max_blocks(sm_count) x kMlpParams floats) added
-// in block order. grad accumulates (+=).
+// in block order. grad accumulates (+=). n_rec records are used (perm[0 ..
+// n_rec) when perm is given); rec_bound is the number of records in the buffer,
+// the bound of a valid perm entry (0: n_rec).
 cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_rec, const float *coef, float dN,
                            float amax, const float *dalpha_direct, float *grad, int sm_count, cudaStream_t s,
-                           const uint32_t *perm, float *partial, int rank2)
+                           const uint32_t *perm, float *partial, int rank2, long long rec_bound)
 {
+    if (rec_bound <= 0) rec_bound = n_rec;
     const size_t smem = sizeof(BwdSmem);
     cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (n_rec <= 0) return cudaSuccess;
     const long long tiles = (n_rec + kBwdRows - 1) / kBwdRows;
     const int grid = (int)std::min<long long>(tiles, (long long)mlp_bwd_max_blocks(sm_count));
-    mlp_bwd_kernel<<<grid, kBwdWarps * 32, smem, s>>>(params, rec, n_rec, coef, -sqrtf(dN), amax,
+    mlp_bwd_kernel<<<grid, kBwdWarps * 32, smem, s>>>(params, rec, n_rec, rec_bound, coef, -sqrtf(dN), amax,
                                                       dalpha_direct, perm, partial, rank2);
     if ((e = cudaGetLastError())) return e;
     mlp_grad_reduce_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(partial, grid, grad);
