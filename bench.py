@@ -743,6 +743,7 @@ def main():
     ap.add_argument("--ref-traj", type=int, default=1 << 15, help="oracle trajectories per step")
     ap.add_argument("--cpu-traj", type=int, default=1 << 18, help="CPU-baseline sample size")
     ap.add_argument("--train-rounds", type=int, default=TRAIN["rounds"])
+    ap.add_argument("--lam", type=float, default=TRAIN["lam"], help="tilt lambda of the training target")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / constant-bias / direct legs")
@@ -773,6 +774,7 @@ def main():
         dist.init_process_group("nccl")
     __graft_entry__.build()
     TRAIN["rounds"] = args.train_rounds
+    TRAIN["lam"] = args.lam
     tail = load_tail()
     N_tail, A_fixed = tail["N_12"], tail["A"]
     m = usr_model()
