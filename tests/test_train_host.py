@@ -78,3 +78,36 @@ def test_selection_stops_run_ids_and_kept_parameters(monkeypatch):
     with pytest.raises(ValueError):
         TR.train_select(None, _prop(), 0, rounds=10, checkpoints=[], val_traj=8, val_seed=1, N_tail=1.0,
                         max_steps=10, dN=1e-3, val_runs=0)
+
+
+def test_batch_rounds_halve_on_overflow_and_number_runs(monkeypatch):
+    """train_batch: proposal k of round r draws Philox run id r K + k on its
+    model; a round whose records overflow is redone on half the paths (all
+    runs alike) and the parameters step once per round; N_cuts may depend on
+    the round."""
+    calls = []
+
+    def fake(ctx, runs, lam, cuts, adam, P, m, v, B, stream=None):
+        calls.append(([r.n_traj for r in runs], [r.run_id for r in runs], [r.model for r in runs], list(cuts)))
+        if runs[0].n_traj > 1000:
+            raise fpt.FptError(fpt.FPT_E_NOMEM, "segment records exceed the record buffer")
+        P += 1.0
+        return [{"loss": 0.5} for _ in runs]
+
+    monkeypatch.setattr(fpt, "fpt_mlp_train_batch", fake)
+    P = torch.zeros((3, 8))
+    B = torch.zeros((3, 16), dtype=torch.uint8)
+    props = [TR.Proposal(params=P[k], blob=B[k], shift=(0.0, 0.0, 0.0), scale=(1.0, 1.0, 1.0), segment=64,
+                         alpha_max=4.0) for k in range(3)]
+    hist = TR.train_batch(None, props, P, B, [2, 0, 1], rounds=2, n_traj=4000, seed=5, lam=0.25,
+                          N_cuts=lambda r: [10.0 + r, 20.0, 30.0], lr=1e-3)
+    assert [c[0][0] for c in calls] == [4000, 2000, 1000, 4000, 2000, 1000]
+    assert calls[0][1] == [0, 1, 2] and calls[3][1] == [3, 4, 5]
+    assert calls[2][2] == [2, 0, 1]
+    assert calls[2][3] == [10.0, 20.0, 30.0] and calls[5][3] == [11.0, 20.0, 30.0]
+    assert float(P[0, 0]) == 2.0 and len(hist) == 2 and [h["round"] for h in props[1].history] == [0, 1]
+    # other errors pass through
+    monkeypatch.setattr(fpt, "fpt_mlp_train_batch",
+                        lambda *a, **k: (_ for _ in ()).throw(fpt.FptError(fpt.FPT_E_CUDA, "launch failed")))
+    with pytest.raises(fpt.FptError):
+        TR.train_batch(None, props, P, B, [0, 0, 0], rounds=1, n_traj=100, seed=5, lam=0.25, N_cuts=[1.0] * 3)
