@@ -632,8 +632,15 @@ cudaError_t mlp_bwd_launch(const float *params, const float *rec, long long n_re
     cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (n_rec <= 0) return cudaSuccess;
+    // one wave: as many blocks as are resident at once (registers allow two per
+    // SM), so no block waits for a second wave; the tile partition, and with it
+    // the gradient, is fixed for a given device
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bwd_kernel, kBwdWarps * 32, smem)))
+        return e;
+    per_sm = std::max(1, std::min(per_sm, 3));
     const long long tiles = (n_rec + kBwdRows - 1) / kBwdRows;
-    const int grid = (int)std::min<long long>(tiles, (long long)mlp_bwd_max_blocks(sm_count));
+    const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sm_count);
     mlp_bwd_kernel<<<grid, kBwdWarps * 32, smem, s>>>(params, rec, n_rec, rec_bound, coef, -sqrtf(dN), amax,
                                                       dalpha_direct, perm, partial, rank2);
     if ((e = cudaGetLastError())) return e;
