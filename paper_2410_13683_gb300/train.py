@@ -38,12 +38,13 @@ class Proposal:
 
 
 def new_proposal(ctx, init_params: np.ndarray, shift, scale, segment: int = 64, alpha_max: float = 4.0,
-                 flags: int = 0, x_floor: float = 0.0):
+                 flags: int = 0, x_floor: float = 0.0, device: str = "cuda"):
     import torch
-    p = torch.tensor(np.asarray(init_params, np.float32), device="cuda")
-    blob = torch.zeros(fpt.FPT_MLP_BLOB_BYTES, dtype=torch.uint8, device="cuda")
+    p = torch.tensor(np.asarray(init_params, np.float32), device=device)
+    blob = torch.zeros(fpt.FPT_MLP_BLOB_BYTES, dtype=torch.uint8, device=device)
     fpt.fpt_mlp_pack(ctx, p, blob)
-    torch.cuda.synchronize()
+    if p.is_cuda:
+        torch.cuda.synchronize()
     return Proposal(p, blob, tuple(float(v) for v in shift), tuple(float(v) for v in scale), segment,
                     alpha_max, flags, float(x_floor))
 
@@ -193,3 +194,32 @@ def train_batch(ctx, props, P, B, models, rounds: int, n_traj: int, seed: int, l
         if log:
             log(st)
     return hist
+
+
+def save_checkpoint(prop: Proposal, path: str) -> None:
+    """Everything a training run needs to resume: the fp32 parameters, the
+    Adam moments, the input normalisation and the per-round history (the
+    next round number is len(history))."""
+    import json
+    import torch
+    m, v = getattr(prop, "_adam", (torch.zeros_like(prop.params), torch.zeros_like(prop.params)))
+    np.savez(path, params=prop.params.detach().cpu().numpy(), adam_m=m.detach().cpu().numpy(),
+             adam_v=v.detach().cpu().numpy(), shift=np.asarray(prop.shift), scale=np.asarray(prop.scale),
+             segment=prop.segment, alpha_max=prop.alpha_max, flags=prop.flags, x_floor=prop.x_floor,
+             history=json.dumps(prop.history))
+
+
+def load_checkpoint(ctx, path: str, device: str = "cuda") -> Proposal:
+    """A proposal saved by save_checkpoint, packed for ctx, with its Adam
+    moments restored: train(..., first_round=len(prop.history)) continues the
+    run as if it had not stopped (rounds are keyed by their number)."""
+    import json
+    import torch
+    z = np.load(path)
+    prop = new_proposal(ctx, z["params"], shift=tuple(z["shift"]), scale=tuple(z["scale"]),
+                        segment=int(z["segment"]), alpha_max=float(z["alpha_max"]), flags=int(z["flags"]),
+                        x_floor=float(z["x_floor"]), device=device)
+    dev = prop.params.device
+    prop._adam = (torch.tensor(z["adam_m"], device=dev), torch.tensor(z["adam_v"], device=dev))
+    prop.history = json.loads(str(z["history"]))
+    return prop

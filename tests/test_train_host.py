@@ -2,7 +2,8 @@
 a round whose segment records overflow the record buffer is redone in
 halves (and the halved chunk is kept), other errors pass through, and the
 held-out selection measures at the right rounds with distinct run ids and
-keeps the best parameters."""
+keeps the best parameters; a checkpointed run resumes exactly."""
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -111,3 +112,40 @@ def test_batch_rounds_halve_on_overflow_and_number_runs(monkeypatch):
                         lambda *a, **k: (_ for _ in ()).throw(fpt.FptError(fpt.FPT_E_CUDA, "launch failed")))
     with pytest.raises(fpt.FptError):
         TR.train_batch(None, props, P, B, [0, 0, 0], rounds=1, n_traj=100, seed=5, lam=0.25, N_cuts=[1.0] * 3)
+
+
+def test_checkpoint_resume_equals_uninterrupted_training(monkeypatch, tmp_path):
+    """Train 3 rounds, save, load into a fresh proposal and train 2 more: the
+    parameters, Adam moments, run ids and history equal those of 5 rounds
+    without the stop."""
+    def fake(ctx, run, chunk, lam, N_cut, adam, params, m, v, blob, stream=None):
+        g = torch.sin(params + float(run.run_id))          # a gradient that depends on the state and the round
+        m.mul_(0.9).add_(0.1 * g)
+        v.mul_(0.999).add_(0.001 * g * g)
+        params.sub_(adam["lr"] * m / (v.sqrt() + 1e-8))
+        return {"loss": float(params.sum()), "run_id": int(run.run_id)}
+
+    monkeypatch.setattr(fpt, "fpt_mlp_train_round", fake)
+    monkeypatch.setattr(fpt, "fpt_mlp_pack", lambda ctx, p, b, stream=None: None)
+
+    def fresh():
+        return TR.new_proposal(None, np.linspace(-1, 1, 8), shift=(0.5, 0.0, 0.0), scale=(0.2, 1.0, 0.01),
+                               segment=128, alpha_max=8.0, flags=fpt.FPT_MLP_LOG_X, x_floor=1e-4,
+                               device="cpu")
+
+    kw = dict(model=0, n_traj=1024, seed=4, lam=0.25, N_cut=lambda r: 10.0 + r)
+    ref = TR.train(None, fresh(), rounds=5, **kw)
+
+    a = TR.train(None, fresh(), rounds=3, **kw)
+    path = str(tmp_path / "ck.npz")
+    TR.save_checkpoint(a, path)
+    b = TR.load_checkpoint(None, path, device="cpu")
+    assert (b.shift, b.scale, b.segment, b.alpha_max, b.flags, b.x_floor) == \
+        (a.shift, a.scale, a.segment, a.alpha_max, a.flags, a.x_floor)
+    assert torch.equal(b.params, a.params) and b.params.dtype == torch.float32
+    assert all(torch.equal(x, y) for x, y in zip(b._adam, a._adam))
+    TR.train(None, b, rounds=2, first_round=len(b.history), **kw)
+    assert [h["run_id"] for h in b.history] == [0, 1, 2, 3, 4]
+    assert [h["round"] for h in b.history] == [h["round"] for h in ref.history]
+    assert torch.equal(b.params, ref.params)
+    assert all(torch.equal(x, y) for x, y in zip(b._adam, ref._adam))
