@@ -249,6 +249,23 @@ __device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restri
            __fdividef(g * d * md.bump_inv_w2, 1.0f + g);
 }
 
+// Passage test on the compensated field: the pair's value x - x_c is <= 0
+// exactly when x <= x_c (without flush-to-zero the rounded difference of two
+// floats is zero or negative only when the exact one is), so the test needs
+// no subtraction.
+__device__ __forceinline__ bool passed(const Lane &L)
+{
+    return L.x <= L.x_c;
+}
+
+// Steps outside the noise window of an N-indexed table (step count below
+// win_lo or above win_hi) are classical.
+template <bool NIDX>
+__device__ __forceinline__ bool outside_window(const Lane &L, int n)
+{
+    return NIDX && L.nidx && (n < L.win_lo || n > L.win_hi);
+}
+
 // One Euler-Maruyama step of Eq. (4.7) with bias amplitude L.cb / sqrt(dN).
 // The field increment (drift + bias + noise) is formed first and added to the
 // compensated field pair: a plain FP32 field would add the same drift
@@ -265,7 +282,7 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     float S = fmaf(f, e.y, e.x);               // S_phiphi sqrt(dN)
     float T = fmaf(f, e.w, e.z);               // tan(theta_n) S_phiphi sqrt(dN)
     float cb = L.cb, half_cb2 = L.half_cb2;
-    if (NIDX && L.nidx && (L.n < L.win_lo || L.n > L.win_hi)) {
+    if (outside_window<NIDX>(L, L.n)) {
         // outside the noise window the step is classical: no noise, no bias, no weight
         S = 0.0f;
         T = 0.0f;
@@ -283,10 +300,25 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
     } else {
         L.p = fmaf(T, zb, fmaf(hh * dN, L.p + vpv, L.p));
     }
-    if (WEIGHTED) L.lw_grp -= fmaf(cb, z, half_cb2);
+    if (WEIGHTED) L.lw_grp -= fmaf(cb, z, half_cb2);   // the step's ln w increment (see group_lw)
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
-    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
+    return passed(L) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
+}
+
+// ln w increments of the first k + 1 steps of a group that starts at step
+// n0, summed as em_step sums them (same operands, same order).
+template <bool NIDX>
+__device__ __forceinline__ float group_lw(const Lane &L, const float (&z)[4], int n0, int k)
+{
+    float lw = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (s > k) break;
+        const bool off = outside_window<NIDX>(L, n0 + s);
+        lw -= fmaf(off ? 0.0f : L.cb, z[s], off ? 0.0f : L.half_cb2);
+    }
+    return lw;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer()
@@ -452,11 +484,11 @@ __device__ __forceinline__ void refill_point(const EmParams &P, Lane &L, bool &a
     const unsigned fin = __ballot_sync(FULL, fin_me);
     if (!fin) return;
     if (fin_me) {
-        const bool passed = __fsub_rn(L.x, L.x_c) <= 0.0f;
+        const bool pas = passed(L);
         P.nsteps[L.unit] = L.n;
         P.logw[L.unit] = (double)L.lw_hi - (double)L.lw_lo;     // the pair holds hi - lo
-        P.status[L.unit] = passed ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
-        if (!passed) atomicAdd(P.flags + 1, 1);
+        P.status[L.unit] = pas ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
+        if (!pas) atomicAdd(P.flags + 1, 1);
     }
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(P.cursor, (unsigned long long)__popc(fin));
@@ -568,25 +600,45 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
             float z[4];
             box_muller(r.x, r.y, z[0], z[1]);
             box_muller(r.z, r.w, z[2], z[3]);
-            // Fast path (single-model launches): when every lane of the warp is
-            // live and so far above the end surface that four steps cannot reach
-            // it -- a step moves the field by at most s_max (|xi| + |alpha| sqrt(dN))
-            // + |pi| dN with |xi| <= 5.77 (the largest Box-Muller radius of a
-            // 23-bit uniform), taken here with a factor 2 to spare -- and four
-            // steps stay below the cap (the step that reaches the cap is taken on
-            // the guarded path, which marks the trajectory capped there), the four
-            // steps run without the per-step
-            // passage test and branch. The arithmetic of a step is the same on
-            // both paths, so results do not depend on which one ran.
-            const bool fast = SMEM &&
-                __all_sync(FULL, active && !done && L.n + 4 < P.m0.max_steps &&
-                                     __fsub_rn(L.x, L.x_c) >
-                                         8.0f * fmaf(P.m0.s_max, 5.8f + fabsf(L.cb), fabsf(L.p) * P.m0.dN));
-            if (fast) {
+            // Speculative group (single-model launches): when every lane of the
+            // warp is live and four steps stay below the cap, the four steps run
+            // without the per-step branch, each lane noting after which steps its
+            // field was at or below the end surface. A lane that passed at step k
+            // of the group then takes the state the guarded path would have left:
+            // k + 1 steps counted, the ln w increments of those steps summed again
+            // from the same operands, its field marked passed (the later steps'
+            // field and momentum are discarded: the trajectory has ended, and only
+            // its step count, weight and status are kept). Results do not depend
+            // on which path ran.
+            if (SMEM && __all_sync(FULL, active && !done && L.n + 4 < P.m0.max_steps)) {
+                const float sx0 = REC ? sg.sum_xi : 0.0f;
+                bool h[4];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
                     if (REC) sg.sum_xi += z[s];
                     em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
+                    h[s] = passed(L);
+                }
+                if (h[0] | h[1] | h[2] | h[3]) {
+                    const int k = h[0] ? 0 : h[1] ? 1 : h[2] ? 2 : 3;
+                    const int n0 = L.n - 4;
+                    // the group's normals again (not kept live through the steps)
+                    const uint4 q = philox4x32_10(make_uint4((uint32_t)n0 >> 2, L.traj, L.run_id, 0u), P.rk);
+                    float zz[4];
+                    box_muller(q.x, q.y, zz[0], zz[1]);
+                    box_muller(q.z, q.w, zz[2], zz[3]);
+                    L.n = n0 + k + 1;
+                    if (WEIGHTED) L.lw_grp = group_lw<NIDX>(L, zz, n0, k);
+                    if (REC) {
+                        float sx = sx0;
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+                            if (s <= k) sx += zz[s];
+                        sg.sum_xi = sx;
+                    }
+                    L.x = -1.0f;
+                    L.x_c = 0.0f;
+                    done = true;
                 }
             } else {
 #pragma unroll
@@ -662,7 +714,7 @@ __device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const floa
     if (WEIGHTED) L.lw_grp -= fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2));
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
-    return (__fsub_rn(L.x, L.x_c) <= 0.0f) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
+    return passed(L) | (L.n >= (SMEM ? M0.max_steps : L.nmax));
 }
 
 // Learned proposal in 2-D: beta = (clamp(o1), clamp(o2)) at the segment start.
