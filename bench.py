@@ -327,7 +327,7 @@ def far_tail_leg(fpt, torch, TR, shard, ctx, prop12, m, tail, n, seed, rank, str
     _t.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3
     sw, sw2 = sum(a for a, _ in sums), sum(b for _, b in sums)
-    sw, sw2 = shard.merge_tail_sums(sw, sw2, dist, device="cuda")
+    sw, sw2 = shard.merge_shards(sw, sw2, rank * n, n, world * n, dist, device="cuda")
     ess = shard.ess_of(sw, sw2)
     n_tot = float(n) * FAR["steps"] * world
     p20 = sw / n_tot
@@ -901,7 +901,7 @@ def main():
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
-    sw_tot, sw2_tot = shard.merge_tail_sums(sw_tot, sw2_tot, dist, device="cuda")
+    sw_tot, sw2_tot = shard.merge_shards(sw_tot, sw2_tot, off, n, world * n, dist, device="cuda")
     ess_total = shard.ess_of(sw_tot, sw2_tot)
     # spread of the pooled ESS over the timed steps (this rank's steps)
     spread = shard.ess_spread([a for a, _ in ess_steps], [b for _, b in ess_steps])
@@ -927,7 +927,7 @@ def main():
         sw_e, sw2_e, _ = pipelined(args.steps, lambda k: k, before=upload)
         torch.cuda.synchronize()
         e2e_t = time.perf_counter() - t0
-        sw_e, sw2_e = shard.merge_tail_sums(sw_e, sw2_e, dist, device="cuda")
+        sw_e, sw2_e = shard.merge_shards(sw_e, sw2_e, off, n, world * n, dist, device="cuda")
         extras["e2e"] = {"value": shard.ess_of(sw_e, sw2_e) / e2e_t, "unit": UNIT,
                          "h2d_bytes_per_step": len(S_pin) * 16 + 128 + (fpt.FPT_MLP_BLOB_BYTES if learned else 0),
                          "d2h_bytes_per_step": (10 * 512 + 16) * 8}
@@ -940,7 +940,7 @@ def main():
         swj, sw2j, stj = pipelined(4, lambda k: k, dfun=jd)     # as pipelined as the learned steps
         torch.cuda.synchronize()
         fixed_t = time.perf_counter() - t0
-        swj, sw2j = shard.merge_tail_sums(swj, sw2j, dist, device="cuda")
+        swj, sw2j = shard.merge_shards(swj, sw2j, rank * nj, nj, world * nj, dist, device="cuda")
         fixed_rate = shard.ess_of(swj, sw2j) / fixed_t
         extras["fixed_bias"] = {"A": A_fixed, "n_traj_per_step": nj, "ess_tail_per_s": fixed_rate,
                                 "timing": "host clock over 4 pipelined steps"}

@@ -543,6 +543,23 @@ fpt_status fpt_histogram_noalloc(const int32_t *nsteps, const double *logw, cons
                                  int64_t n, double dN, double N_lo, double N_hi, int32_t n_bins,
                                  double N_tail, double *out, void *cuda_stream);
 
+/* Capped allocator: the device memory the context allocates (trajectory
+ * outputs, tables, histogram, record and training scratch) is counted, and
+ * from this call on an allocation that would take the count past max_bytes
+ * fails as an out-of-memory cudaMalloc does: the call that needed it returns
+ * FPT_E_NOMEM (fpt_last_error names the limit, the bytes in use and the bytes
+ * requested), and the context stays usable -- a later call with a smaller
+ * request, or after the limit is raised, succeeds. Memory already held is
+ * kept. max_bytes = 0 removes the limit (the default); negative values are
+ * FPT_E_INVALID. Serves memory budgeting beside other users of the GPU and
+ * the injection of allocation failures.
+ */
+fpt_status fpt_set_memory_limit(fpt_ctx *ctx, int64_t max_bytes);
+
+/* Device bytes the context holds now (*in_use) and its limit (*max_bytes,
+ * 0 = none); either pointer may be NULL. */
+fpt_status fpt_memory_in_use(const fpt_ctx *ctx, int64_t *in_use, int64_t *max_bytes);
+
 /* Release everything the context owns. NULL is allowed. */
 void fpt_destroy(fpt_ctx *ctx);
 

@@ -17,6 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfpt.so")
+# debug build with the device bounds checks (-DFPT_CHECKS); loaded when the
+# environment sets FPT_CHECKS=1
+LIB_CHECKS = os.path.join(PKG, "libfpt_checks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["fpt_kernels.cu", "fpt_abi.cu", "fpt_mlp.cu"]
@@ -42,22 +45,29 @@ def _deps():
     return out
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(checks: bool = False) -> bool:
+    lib = LIB_CHECKS if checks else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Build libfpt.so, or with checks=True libfpt_checks.so (device bounds
+    checks compiled in, -DFPT_CHECKS); returns the library's path."""
+    lib = LIB_CHECKS if checks else LIB
+    if not force and not needs_build(checks):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = os.path.join(BUILD, "checks") if checks else BUILD
+    os.makedirs(bdir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if checks:
+        common.append("-DFPT_CHECKS")
     procs, objs = [], []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
             cmd = [nvcc] + ARCH + ["-lineinfo"] + common + ["-c", src, "-o", obj]
         else:
@@ -75,14 +85,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(out.decode(errors="replace"), file=sys.stderr)
     if failed:
         raise RuntimeError("libfpt build failed:\n" + "\n".join(f"{s}:\n{o}" for s, o in failed))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("libfpt link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checks="--checks" in sys.argv))

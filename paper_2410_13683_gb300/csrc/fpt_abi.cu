@@ -9,10 +9,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -74,7 +76,7 @@ struct fpt_ctx {
     RunDev *d_runs = nullptr;
     RunDev *h_runs = nullptr;           // pinned staging
     unsigned long long *d_cursor = nullptr;
-    int *d_flags = nullptr;             // [0] abort, [1] capped
+    int *d_flags = nullptr;             // launch flag words (kFlag* in fpt_internal.h)
     int *h_flags = nullptr;             // pinned copy
     int32_t *d_nsteps = nullptr;
     double *d_logw = nullptr;
@@ -127,6 +129,12 @@ struct fpt_ctx {
     long long *d_off = nullptr;
     long long off_cap = 0;
     int *d_rec_err = nullptr;
+
+    // device memory of the context, counted against an optional limit
+    std::unordered_map<void *, size_t> dev_sizes;
+    size_t dev_bytes = 0;
+    size_t dev_limit = 0;           // 0: no limit
+    size_t refused_bytes = 0;       // last request the limit refused
 };
 
 static fpt_status fail(fpt_ctx *c, fpt_status s, const std::string &msg)
@@ -142,7 +150,59 @@ static fpt_status fail(fpt_ctx *c, fpt_status s, const std::string &msg)
 static fpt_status cuda_fail(fpt_ctx *c, cudaError_t e, const char *what)
 {
     fpt_status s = (e == cudaErrorMemoryAllocation) ? FPT_E_NOMEM : FPT_E_CUDA;
-    return fail(c, s, std::string(what) + ": " + cudaGetErrorString(e));
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (c && e == cudaErrorMemoryAllocation && c->refused_bytes) {
+        msg += " (context memory limit " + std::to_string(c->dev_limit) + " bytes: " +
+               std::to_string(c->dev_bytes) + " in use, " + std::to_string(c->refused_bytes) + " requested)";
+        c->refused_bytes = 0;
+    }
+    return fail(c, s, msg);
+}
+
+#ifdef FPT_CHECKS
+// A failed device bounds check makes the call that observes it (fpt_sync, a
+// histogram) return FPT_E_STATE.
+static fpt_status take_checks(fpt_ctx *c)
+{
+    int word = 0;
+    const cudaError_t e = checks_take(&word);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the bounds-check word");
+    if (!word) return FPT_OK;
+    std::string what;
+    if (word & kCheckTable) what += " noise-table index;";
+    if (word & kCheckDriftTable) what += " drift-table index;";
+    if (word & kCheckUnit) what += " trajectory index;";
+    if (word & kCheckBin) what += " histogram bin;";
+    return fail(c, FPT_E_STATE, "device bounds check failed (FPT_CHECKS):" + what + " results are invalid");
+}
+#endif
+
+// Device allocations of a context: counted, and refused like an out-of-memory
+// cudaMalloc when they would take the context past its limit.
+template <class T>
+static cudaError_t dev_malloc(fpt_ctx *ctx, T **p, size_t bytes)
+{
+    if (ctx->dev_limit && ctx->dev_bytes + bytes > ctx->dev_limit) {
+        ctx->refused_bytes = bytes;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+    if (e == cudaSuccess) {
+        ctx->dev_sizes[*p] = bytes;
+        ctx->dev_bytes += bytes;
+    }
+    return e;
+}
+
+static void dev_free(fpt_ctx *ctx, void *p)
+{
+    if (!p) return;
+    auto it = ctx->dev_sizes.find(p);
+    if (it != ctx->dev_sizes.end()) {
+        ctx->dev_bytes -= it->second;
+        ctx->dev_sizes.erase(it);
+    }
+    cudaFree(p);
 }
 
 #define CK(call)                                              \
@@ -166,37 +226,37 @@ static void free_all(fpt_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     clear_graphs(ctx);
-    cudaFree(ctx->d_models);
-    cudaFree(ctx->d_tables);
-    cudaFree(ctx->d_runs);
+    dev_free(ctx, ctx->d_models);
+    dev_free(ctx, ctx->d_tables);
+    dev_free(ctx, ctx->d_runs);
     cudaFreeHost(ctx->h_runs);
-    cudaFree(ctx->d_cursor);
-    cudaFree(ctx->d_flags);
+    dev_free(ctx, ctx->d_cursor);
+    dev_free(ctx, ctx->d_flags);
     cudaFreeHost(ctx->h_flags);
-    cudaFree(ctx->d_nsteps);
-    cudaFree(ctx->d_logw);
-    cudaFree(ctx->d_status);
-    cudaFree(ctx->d_N);
-    cudaFree(ctx->d_hmax);
-    cudaFree(ctx->d_hmom);
-    cudaFree(ctx->d_hscal);
-    cudaFree(ctx->d_hout);
+    dev_free(ctx, ctx->d_nsteps);
+    dev_free(ctx, ctx->d_logw);
+    dev_free(ctx, ctx->d_status);
+    dev_free(ctx, ctx->d_N);
+    dev_free(ctx, ctx->d_hmax);
+    dev_free(ctx, ctx->d_hmom);
+    dev_free(ctx, ctx->d_hscal);
+    dev_free(ctx, ctx->d_hout);
     cudaFreeHost(ctx->h_hout);
-    cudaFree(ctx->d_records);
-    cudaFree(ctx->d_rec_cursor);
-    cudaFree(ctx->d_Y);
-    cudaFree(ctx->d_coef);
-    cudaFree(ctx->d_acc);
-    cudaFree(ctx->d_grad);
-    cudaFree(ctx->d_tmp);
-    cudaFree(ctx->d_gpart);
-    cudaFree(ctx->d_perm);
-    cudaFree(ctx->d_cnt);
-    cudaFree(ctx->d_off);
-    cudaFree(ctx->d_rec_err);
-    cudaFree(ctx->d_xn);
-    cudaFree(ctx->d_xlw);
-    cudaFree(ctx->d_xst);
+    dev_free(ctx, ctx->d_records);
+    dev_free(ctx, ctx->d_rec_cursor);
+    dev_free(ctx, ctx->d_Y);
+    dev_free(ctx, ctx->d_coef);
+    dev_free(ctx, ctx->d_acc);
+    dev_free(ctx, ctx->d_grad);
+    dev_free(ctx, ctx->d_tmp);
+    dev_free(ctx, ctx->d_gpart);
+    dev_free(ctx, ctx->d_perm);
+    dev_free(ctx, ctx->d_cnt);
+    dev_free(ctx, ctx->d_off);
+    dev_free(ctx, ctx->d_rec_err);
+    dev_free(ctx, ctx->d_xn);
+    dev_free(ctx, ctx->d_xlw);
+    dev_free(ctx, ctx->d_xst);
     if (ctx->run_done) cudaEventDestroy(ctx->run_done);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
 }
@@ -208,10 +268,10 @@ static fpt_status ensure_dev(fpt_ctx *ctx, T *&ptr, long long &cap, long long ne
 {
     if (need <= cap) return FPT_OK;
     CK(cudaStreamSynchronize(ctx->stream));
-    cudaFree(ptr);
+    dev_free(ctx, ptr);
     ptr = nullptr;
     cap = 0;
-    CK(cudaMalloc(&ptr, sizeof(T) * need));
+    CK(dev_malloc(ctx, &ptr, sizeof(T) * need));
     cap = need;
     return FPT_OK;
 }
@@ -233,7 +293,11 @@ __global__ void grad_norm_kernel(const float *g, int n, double *out)
 
 extern "C" {
 
+#ifdef FPT_CHECKS
+const char *fpt_version(void) { return "fpt-gb300 0.1 (sm_103a, FPT_CHECKS)"; }
+#else
 const char *fpt_version(void) { return "fpt-gb300 0.1 (sm_103a)"; }
+#endif
 
 const char *fpt_last_error(const fpt_ctx *ctx)
 {
@@ -546,16 +610,16 @@ fpt_status fpt_init_model(fpt_ctx **pctx, const fpt_model *models, int32_t n_mod
     if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device))) return bail(e, "attribute");
     if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking))) return bail(e, "stream");
     if ((e = cudaEventCreateWithFlags(&ctx->run_done, cudaEventDisableTiming))) return bail(e, "event");
-    if ((e = cudaMalloc(&ctx->d_models, sizeof(ModelDev) * kMaxModels))) return bail(e, "cudaMalloc models");
-    if ((e = cudaMalloc(&ctx->d_runs, sizeof(RunDev) * kMaxRuns))) return bail(e, "cudaMalloc runs");
+    if ((e = dev_malloc(ctx, &ctx->d_models, sizeof(ModelDev) * kMaxModels))) return bail(e, "cudaMalloc models");
+    if ((e = dev_malloc(ctx, &ctx->d_runs, sizeof(RunDev) * kMaxRuns))) return bail(e, "cudaMalloc runs");
     if ((e = cudaMallocHost(&ctx->h_runs, sizeof(RunDev) * kMaxRuns))) return bail(e, "cudaMallocHost runs");
-    if ((e = cudaMalloc(&ctx->d_cursor, 64))) return bail(e, "cudaMalloc cursor");
-    if ((e = cudaMalloc(&ctx->d_flags, 64))) return bail(e, "cudaMalloc flags");
+    if ((e = dev_malloc(ctx, &ctx->d_cursor, 64))) return bail(e, "cudaMalloc cursor");
+    if ((e = dev_malloc(ctx, &ctx->d_flags, 64))) return bail(e, "cudaMalloc flags");
     if ((e = cudaMallocHost(&ctx->h_flags, 64))) return bail(e, "cudaMallocHost flags");
-    if ((e = cudaMalloc(&ctx->d_hmax, sizeof(unsigned long long) * (kMaxBins + 2)))) return bail(e, "cudaMalloc hist");
-    if ((e = cudaMalloc(&ctx->d_hmom, sizeof(double) * (size_t)kJackknife * kMaxBins * 5))) return bail(e, "cudaMalloc hist");
-    if ((e = cudaMalloc(&ctx->d_hscal, sizeof(double) * kJackknife * 16))) return bail(e, "cudaMalloc hist");
-    if ((e = cudaMalloc(&ctx->d_hout, sizeof(double) * hout_doubles()))) return bail(e, "cudaMalloc hist");
+    if ((e = dev_malloc(ctx, &ctx->d_hmax, sizeof(unsigned long long) * (kMaxBins + 2)))) return bail(e, "cudaMalloc hist");
+    if ((e = dev_malloc(ctx, &ctx->d_hmom, sizeof(double) * (size_t)kJackknife * kMaxBins * 5))) return bail(e, "cudaMalloc hist");
+    if ((e = dev_malloc(ctx, &ctx->d_hscal, sizeof(double) * kJackknife * 16))) return bail(e, "cudaMalloc hist");
+    if ((e = dev_malloc(ctx, &ctx->d_hout, sizeof(double) * hout_doubles()))) return bail(e, "cudaMalloc hist");
     if ((e = cudaMallocHost(&ctx->h_hout, sizeof(double) * hout_doubles()))) return bail(e, "cudaMallocHost hist");
     std::memset(ctx->h_flags, 0, 64);
     *pctx = ctx;
@@ -655,6 +719,8 @@ static fpt_status upload_tables(fpt_ctx *ctx)
         }
         d.dN = (float)m.dN;
         d.sqrt_dN = (float)std::sqrt(m.dN);
+        d.half_dN = 0.5f * d.dN;       // the same FP32 products the steppers form from dN
+        d.m3dN = -3.0f * d.dN;
         d.max_steps = (int32_t)m.max_steps;
         d.table_offset = ctx->table_offset[i];
         if (t.ready) {
@@ -681,11 +747,6 @@ static fpt_status upload_tables(fpt_ctx *ctx)
             }
             const double sq = std::sqrt(m.dN);
             d.rank2 = t.rank2 ? 1 : 0;
-            // bound of a step's field noise per unit normal: S_phiphi (1-D), S_phiphi + |S_phipi| (2-D)
-            double smax = 0.0;
-            for (int j = 0; j < t.M; ++j)
-                smax = std::max(smax, (std::fabs(t.S[j]) + (t.rank2 ? std::fabs(t.T[j]) : 0.0)) * sq);
-            d.s_max = (float)(smax * (1.0 + 1e-6));
             if (t.rank2) {
                 // (S_phiphi, S_phipi, S_pipi, 0) sqrt(dN); entry M repeats entry M - 1
                 for (int j = 0; j <= t.M; ++j) {
@@ -707,10 +768,10 @@ static fpt_status upload_tables(fpt_ctx *ctx)
         }
     }
     if (packed.size() > ctx->tables_cap) {
-        cudaFree(ctx->d_tables);
+        dev_free(ctx, ctx->d_tables);
         ctx->d_tables = nullptr;
         ctx->tables_cap = 0;
-        CK(cudaMalloc(&ctx->d_tables, sizeof(float4) * packed.size()));
+        CK(dev_malloc(ctx, &ctx->d_tables, sizeof(float4) * packed.size()));
         ctx->tables_cap = packed.size();
         clear_graphs(ctx);
     }
@@ -790,19 +851,35 @@ fpt_status fpt_get_launch(const fpt_ctx *ctx, fpt_launch *l)
     return FPT_OK;
 }
 
+fpt_status fpt_set_memory_limit(fpt_ctx *ctx, int64_t max_bytes)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (max_bytes < 0) return fail(ctx, FPT_E_INVALID, "memory limit must be >= 0");
+    ctx->dev_limit = (size_t)max_bytes;
+    return FPT_OK;
+}
+
+fpt_status fpt_memory_in_use(const fpt_ctx *ctx, int64_t *in_use, int64_t *max_bytes)
+{
+    if (!ctx) return FPT_E_INVALID;
+    if (in_use) *in_use = (int64_t)ctx->dev_bytes;
+    if (max_bytes) *max_bytes = (int64_t)ctx->dev_limit;
+    return FPT_OK;
+}
+
 static fpt_status ensure_units(fpt_ctx *ctx, long long total)
 {
     if (total <= ctx->unit_cap) return FPT_OK;
     long long cap = std::max<long long>(total, 1 << 16);
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
-    cudaFree(ctx->d_nsteps); cudaFree(ctx->d_logw); cudaFree(ctx->d_status); cudaFree(ctx->d_N);
+    dev_free(ctx, ctx->d_nsteps); dev_free(ctx, ctx->d_logw); dev_free(ctx, ctx->d_status); dev_free(ctx, ctx->d_N);
     ctx->d_nsteps = nullptr; ctx->d_logw = nullptr; ctx->d_status = nullptr; ctx->d_N = nullptr;
     ctx->unit_cap = 0;
     clear_graphs(ctx);
-    CK(cudaMalloc(&ctx->d_nsteps, sizeof(int32_t) * cap));
-    CK(cudaMalloc(&ctx->d_logw, sizeof(double) * cap));
-    CK(cudaMalloc(&ctx->d_status, cap));
+    CK(dev_malloc(ctx, &ctx->d_nsteps, sizeof(int32_t) * cap));
+    CK(dev_malloc(ctx, &ctx->d_logw, sizeof(double) * cap));
+    CK(dev_malloc(ctx, &ctx->d_status, cap));
     ctx->unit_cap = cap;
     return FPT_OK;
 }
@@ -821,7 +898,7 @@ static cudaError_t enqueue_run(fpt_ctx *ctx, const EmParams &p, EmVariant v, int
     if ((e = cudaMemsetAsync(ctx->d_status, FPT_TRAJ_ABORTED, (size_t)p.total_units, s))) return e;
     if (v.rec && (e = cudaMemsetAsync(ctx->d_rec_cursor, 0, sizeof(unsigned long long), s))) return e;
     if ((e = em_launch(p, v, grid, block, smem_bytes, s))) return e;
-    return cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    return cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, kFlagWords * sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_traj_out *out,
@@ -991,7 +1068,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
     p.rec_cursor = ctx->d_rec_cursor;
     p.rec_cap = ctx->rec_cap;
     p.budget_ns = ctx->launch.deadline_s > 0.0 ? (unsigned long long)(ctx->launch.deadline_s * 1e9) + 1ull : 0ull;
-    p.t0 = reinterpret_cast<unsigned long long *>(ctx->d_flags + 2);   // zeroed with the flags
+    p.t0 = reinterpret_cast<unsigned long long *>(ctx->d_flags + kFlagT0);   // zeroed with the flags
     const bool graph = ctx->launch.use_graph && p.budget_ns == 0;
 
     if (total > 0) {
@@ -1048,7 +1125,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             if (e != cudaSuccess) return cuda_fail(ctx, e, "run launch");
         }
     } else {
-        std::memset(ctx->h_flags, 0, 4 * sizeof(int));
+        std::memset(ctx->h_flags, 0, kFlagWords * sizeof(int));
     }
     CK(cudaEventRecord(ctx->run_done, s));
     ctx->last_n_runs = n_runs;
@@ -1067,7 +1144,7 @@ fpt_status fpt_run(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n_runs, fpt_t
             if (o.logw) CK(cudaMemcpyAsync(o.logw, ctx->d_logw + rd.unit_begin, sizeof(double) * n, cudaMemcpyDefault, s));
             if (o.status) CK(cudaMemcpyAsync(o.status, ctx->d_status + rd.unit_begin, n, cudaMemcpyDefault, s));
             if (o.N) {
-                if (!ctx->d_N) CK(cudaMalloc(&ctx->d_N, sizeof(double) * ctx->unit_cap));
+                if (!ctx->d_N) CK(dev_malloc(ctx, &ctx->d_N, sizeof(double) * ctx->unit_cap));
                 CK(n_of_steps_launch(ctx->d_nsteps + rd.unit_begin, n, ctx->models[rd.model].dN,
                                      ctx->d_N + rd.unit_begin, s));
                 CK(cudaMemcpyAsync(o.N, ctx->d_N + rd.unit_begin, sizeof(double) * n, cudaMemcpyDefault, s));
@@ -1090,6 +1167,12 @@ fpt_status fpt_sync(fpt_ctx *ctx)
     CK(cudaSetDevice(ctx->device));
     if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
     CK(cudaStreamSynchronize(ctx->stream));
+#ifdef FPT_CHECKS
+    {
+        const fpt_status cs = take_checks(ctx);
+        if (cs != FPT_OK) return cs;
+    }
+#endif
     if (!ctx->last_valid) return FPT_OK;
     if (ctx->h_flags[0]) return fail(ctx, FPT_E_TIMEOUT, "kernel deadline passed; run aborted");
     if (ctx->h_flags[1] > 0) {
@@ -1104,6 +1187,8 @@ static fpt_status hist_args(fpt_ctx *ctx, double N_lo, double N_hi, int32_t n_bi
     if (n_bins < 1 || n_bins > kMaxBins) return fail(ctx, FPT_E_INVALID, "n_bins out of [1, 4096]");
     if (!(N_hi > N_lo) || !std::isfinite(N_lo) || !std::isfinite(N_hi))
         return fail(ctx, FPT_E_INVALID, "need finite N_lo < N_hi");
+    if (!((N_hi - N_lo) / n_bins >= DBL_MIN) || !std::isfinite(N_hi - N_lo))
+        return fail(ctx, FPT_E_INVALID, "bin width (N_hi - N_lo) / n_bins must be a positive normal number");
     if (!std::isnan(N_tail) && !std::isfinite(N_tail)) return fail(ctx, FPT_E_INVALID, "N_tail must be finite or NaN");
     return FPT_OK;
 }
@@ -1136,6 +1221,12 @@ static fpt_status hist_run(fpt_ctx *ctx, const int32_t *nsteps, const double *lo
     const size_t nd = (size_t)10 * n_bins + 16;
     CK(cudaMemcpyAsync(ctx->h_hout, ctx->d_hout, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+#ifdef FPT_CHECKS
+    {
+        const fpt_status cs = take_checks(ctx);
+        if (cs != FPT_OK) return cs;
+    }
+#endif
     const double *h = ctx->h_hout;
     for (int b = 0; b < n_bins; ++b) {
         if (out->count) out->count[b] = (int64_t)h[b];
@@ -1208,11 +1299,11 @@ fpt_status fpt_histogram_data(fpt_ctx *ctx, const int32_t *nsteps, const double 
     if (!dev) {
         if (n > ctx->x_cap) {
             CK(cudaStreamSynchronize(s));
-            cudaFree(ctx->d_xn); cudaFree(ctx->d_xlw); cudaFree(ctx->d_xst);
+            dev_free(ctx, ctx->d_xn); dev_free(ctx, ctx->d_xlw); dev_free(ctx, ctx->d_xst);
             ctx->d_xn = nullptr; ctx->d_xlw = nullptr; ctx->d_xst = nullptr; ctx->x_cap = 0;
-            CK(cudaMalloc(&ctx->d_xn, sizeof(int32_t) * n));
-            CK(cudaMalloc(&ctx->d_xlw, sizeof(double) * n));
-            CK(cudaMalloc(&ctx->d_xst, n));
+            CK(dev_malloc(ctx, &ctx->d_xn, sizeof(int32_t) * n));
+            CK(dev_malloc(ctx, &ctx->d_xlw, sizeof(double) * n));
+            CK(dev_malloc(ctx, &ctx->d_xst, n));
             ctx->x_cap = n;
         }
         CK(cudaMemcpyAsync(ctx->d_xn, nsteps, sizeof(int32_t) * n, cudaMemcpyDefault, s));
@@ -1304,7 +1395,7 @@ fpt_status fpt_mlp_pack(fpt_ctx *ctx, const float *params, void *blob, void *cud
 static fpt_status ensure_gpart(fpt_ctx *ctx)
 {
     if (ctx->d_gpart) return FPT_OK;
-    CK(cudaMalloc(&ctx->d_gpart, sizeof(float) * (size_t)mlp_bwd_max_blocks(ctx->sm_count) * kMlpParams));
+    CK(dev_malloc(ctx, &ctx->d_gpart, sizeof(float) * (size_t)mlp_bwd_max_blocks(ctx->sm_count) * kMlpParams));
     return FPT_OK;
 }
 
@@ -1404,14 +1495,14 @@ fpt_status fpt_run_records(fpt_ctx *ctx, const fpt_run_desc *run, int64_t cap, f
                                                1LL << 29);
     if (want > ctx->rec_cap) {
         CK(cudaStreamSynchronize(s));
-        cudaFree(ctx->d_records);
+        dev_free(ctx, ctx->d_records);
         ctx->d_records = nullptr;
         ctx->rec_cap = 0;
         clear_graphs(ctx);
-        CK(cudaMalloc(&ctx->d_records, sizeof(float) * 8 * want));
+        CK(dev_malloc(ctx, &ctx->d_records, sizeof(float) * 8 * want));
         ctx->rec_cap = want;
     }
-    if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
+    if (!ctx->d_rec_cursor) CK(dev_malloc(ctx, &ctx->d_rec_cursor, 64));
     ctx->record_mode = true;
     fpt_status st = fpt_run(ctx, run, 1, nullptr, s);
     ctx->record_mode = false;
@@ -1451,17 +1542,17 @@ fpt_status fpt_mlp_train_round(fpt_ctx *ctx, const fpt_run_desc *run, int64_t ch
     const long long want = std::min<long long>(ch * seg_per_traj, 1LL << 29);
     if (want > ctx->rec_cap) {
         CK(cudaStreamSynchronize(s));
-        cudaFree(ctx->d_records);
+        dev_free(ctx, ctx->d_records);
         ctx->d_records = nullptr;
         ctx->rec_cap = 0;
         clear_graphs(ctx);
-        CK(cudaMalloc(&ctx->d_records, sizeof(float) * 8 * want));
+        CK(dev_malloc(ctx, &ctx->d_records, sizeof(float) * 8 * want));
         ctx->rec_cap = want;
     }
-    if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
-    if (!ctx->d_acc) CK(cudaMalloc(&ctx->d_acc, sizeof(double) * mlp_coef_scratch_doubles()));
-    if (!ctx->d_grad) CK(cudaMalloc(&ctx->d_grad, sizeof(float) * kMlpParams));
-    if (!ctx->d_rec_err) CK(cudaMalloc(&ctx->d_rec_err, 64));
+    if (!ctx->d_rec_cursor) CK(dev_malloc(ctx, &ctx->d_rec_cursor, 64));
+    if (!ctx->d_acc) CK(dev_malloc(ctx, &ctx->d_acc, sizeof(double) * mlp_coef_scratch_doubles()));
+    if (!ctx->d_grad) CK(dev_malloc(ctx, &ctx->d_grad, sizeof(float) * kMlpParams));
+    if (!ctx->d_rec_err) CK(dev_malloc(ctx, &ctx->d_rec_err, 64));
     fpt_status st = ensure_dev(ctx, ctx->d_coef, ctx->coef_cap, ch);
     if (st != FPT_OK) return st;
     if ((st = ensure_dev(ctx, ctx->d_Y, ctx->y_cap, ch)) != FPT_OK) return st;
@@ -1568,16 +1659,16 @@ fpt_status fpt_mlp_train_batch(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n
     want = std::min<long long>(want, 1LL << 29);
     if (want > ctx->rec_cap) {
         CK(cudaStreamSynchronize(s));
-        cudaFree(ctx->d_records);
+        dev_free(ctx, ctx->d_records);
         ctx->d_records = nullptr;
         ctx->rec_cap = 0;
         clear_graphs(ctx);
-        CK(cudaMalloc(&ctx->d_records, sizeof(float) * 8 * want));
+        CK(dev_malloc(ctx, &ctx->d_records, sizeof(float) * 8 * want));
         ctx->rec_cap = want;
     }
     const size_t acc_doubles = mlp_coef_scratch_doubles();
-    if (!ctx->d_rec_cursor) CK(cudaMalloc(&ctx->d_rec_cursor, 64));
-    if (!ctx->d_rec_err) CK(cudaMalloc(&ctx->d_rec_err, 64));
+    if (!ctx->d_rec_cursor) CK(dev_malloc(ctx, &ctx->d_rec_cursor, 64));
+    if (!ctx->d_rec_err) CK(dev_malloc(ctx, &ctx->d_rec_err, 64));
     fpt_status st;
     if ((st = ensure_dev(ctx, ctx->d_coef, ctx->coef_cap, total)) != FPT_OK) return st;
     if ((st = ensure_dev(ctx, ctx->d_Y, ctx->y_cap, total)) != FPT_OK) return st;
@@ -1587,8 +1678,8 @@ fpt_status fpt_mlp_train_batch(fpt_ctx *ctx, const fpt_run_desc *runs, int32_t n
     if ((st = ensure_dev(ctx, ctx->d_tmp, ctx->tmp_cap, (long long)n_runs * kMlpParams)) != FPT_OK) return st;
     if ((st = ensure_gpart(ctx)) != FPT_OK) return st;
     double *d_accs = nullptr;
-    CK(cudaMalloc(&d_accs, sizeof(double) * acc_doubles * n_runs));
-    struct Free { double *p; ~Free() { cudaFree(p); } } free_accs{d_accs};
+    CK(dev_malloc(ctx, &d_accs, sizeof(double) * acc_doubles * n_runs));
+    struct Free { fpt_ctx *c; double *p; ~Free() { dev_free(c, p); } } free_accs{ctx, d_accs};
 
     // one launch generates every run's paths with segment records
     ctx->record_mode = true;
@@ -1670,6 +1761,8 @@ fpt_status fpt_histogram_noalloc(const int32_t *nsteps, const double *logw, cons
     if (!(dN > 0) || !std::isfinite(dN)) return fail(nullptr, FPT_E_INVALID, "dN must be positive");
     if (!(N_hi > N_lo) || !std::isfinite(N_lo) || !std::isfinite(N_hi))
         return fail(nullptr, FPT_E_INVALID, "need finite N_lo < N_hi");
+    if (!((N_hi - N_lo) / n_bins >= DBL_MIN) || !std::isfinite(N_hi - N_lo))
+        return fail(nullptr, FPT_E_INVALID, "bin width (N_hi - N_lo) / n_bins must be a positive normal number");
     if (!std::isnan(N_tail) && !std::isfinite(N_tail)) return fail(nullptr, FPT_E_INVALID, "N_tail must be finite or NaN");
     HistParams p;
     std::memset(&p, 0, sizeof(p));

@@ -41,6 +41,22 @@ constexpr int kNoAllocMaxBins = 1024;   // fpt_histogram_noalloc
 constexpr int kMlpHidden = 64;
 constexpr int kMlpMaxBlock = 384;       // block-size cap of the learned-proposal steppers
 
+// Flag words of a stepper launch (64 bytes of device memory, zeroed before
+// the launch; the first kFlagWords ints are read back after it).
+constexpr int kFlagAbort = 0;        // the deadline passed
+constexpr int kFlagCapped = 1;       // trajectories that hit max_steps
+constexpr int kFlagRecOverflow = 3;  // segment records past the record buffer
+constexpr int kFlagChecks = 4;       // FPT_CHECKS builds: failed bounds checks (kCheck* bits)
+constexpr int kFlagWords = 5;
+constexpr int kFlagT0 = 8;           // ints 8-9: the launch's clock origin (64-bit)
+
+// Bits of the FPT_CHECKS error word.
+constexpr int kCheckTable = 1;       // noise-table entry index
+constexpr int kCheckDriftTable = 2;  // drift-table entry index
+constexpr int kCheckUnit = 4;        // trajectory (output) index from the work cursor
+constexpr int kCheckBin = 8;         // histogram bin
+
+
 // Model constants in the shifted coordinate x = phi - phi_end (FP32).
 struct ModelDev {
     float x_star;              // phi_star - phi_end (FP32 head)
@@ -64,7 +80,7 @@ struct ModelDev {
     float d_umax;              // intervals of the drift table
     float bump_m2, bump_phi_end, bump_dphi0, bump_inv_w2, bump_K;
     int32_t win_lo, win_hi;    // noise window [win_lo, win_hi] in steps (nidx)
-    float s_max;               // max of S_phiphi sqrt(dN) over the table (bound of a step's noise)
+    float half_dN, m3dN;       // 0.5 dN and -3 dN in FP32 (momentum drift)
 };
 
 // One run of a launch (FP32 constants; 64-bit unit bookkeeping).
@@ -101,7 +117,7 @@ struct EmParams {
     int smem_table_points;     // SMEM mode: entries staged
     long long total_units;
     unsigned long long *cursor;
-    int *flags;                // [0] abort, [1] capped count
+    int *flags;                // flag words (kFlag*)
     int32_t *nsteps;
     double *logw;
     uint8_t *status;
@@ -150,6 +166,9 @@ struct EmVariant {
 // Host wrappers implemented in fpt_kernels.cu.
 int em_occupancy(EmVariant v, int block, size_t smem_bytes);
 size_t em_smem_bytes(EmVariant v, int table_entries, int n_runs, int n_models);
+// FPT_CHECKS builds: read and clear the device error word of the bounds checks
+// (kCheck* bits; synchronous). Other builds return 0.
+cudaError_t checks_take(int *word);
 cudaError_t em_launch(const EmParams &p, EmVariant v, int grid, int block, size_t smem_bytes,
                       cudaStream_t s);
 

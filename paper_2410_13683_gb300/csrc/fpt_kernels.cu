@@ -27,6 +27,37 @@
 
 namespace fpt_dev {
 
+// Device bounds checks of FPT_CHECKS builds: a failed check sets its bit
+// (kCheck*) in the error word and redirects the access to a valid index; the
+// kernel carries on (warp-synchronous code cannot leave early), and the host
+// reads and clears the word after each run or histogram (checks_take) and
+// turns it into FPT_E_STATE. Other builds compile the checks away.
+#ifdef FPT_CHECKS
+__device__ int g_check_word;
+#define CHECK_INDEX(idx, n, bit)                        \
+    do {                                                \
+        if ((idx) < 0 || (idx) >= (n)) {                \
+            atomicOr(&g_check_word, (bit));             \
+            (idx) = 0;                                  \
+        }                                               \
+    } while (0)
+#else
+#define CHECK_INDEX(idx, n, bit) do {} while (0)
+#endif
+
+cudaError_t checks_take(int *word)
+{
+    *word = 0;
+#ifdef FPT_CHECKS
+    cudaError_t e = cudaMemcpyFromSymbol(word, g_check_word, sizeof(int));
+    if (e != cudaSuccess) return e;
+    const int zero = 0;
+    return cudaMemcpyToSymbol(g_check_word, &zero, sizeof(int));
+#else
+    return cudaSuccess;
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 // ---------------------------------------------------------------------------
@@ -76,7 +107,7 @@ __device__ __forceinline__ void box_muller(uint32_t r0, uint32_t r1, float &z0, 
 {
     const float u0 = uniform23(r0);
     const float u1 = uniform23(r1);
-    const float rho = sqrt_approx(fmaxf(-2.0f * __logf(u0), 0.0f));
+    const float rho = sqrt_approx(fmaxf(-1.38629436111989061f * __log2f(u0), 0.0f));   // -2 ln u0
     float sn, cs;
     __sincosf(fmaf(u1, 6.28318530717958648f, -3.14159265358979324f), &sn, &cs);
     z0 = -rho * cs;
@@ -122,6 +153,7 @@ struct Lane {                // per-thread trajectory state and its constants
     } dc;
     float u_scale, u_shift, u_max;
     int tbase;
+    int M;                   // noise-table points of the lane's model (bounds checks)
     bool mlp;
     bool nidx;               // noise table indexed by the step count
     int win_lo, win_hi;      // noise window in steps (nidx)
@@ -173,6 +205,7 @@ __device__ __forceinline__ void lane_load(Lane &L, long long unit, const RunSm *
     L.u_shift = m.u_shift;
     L.u_max = m.u_umax;
     L.tbase = m.table_offset;
+    L.M = m.M;
     L.nidx = m.nidx != 0;
     L.win_lo = m.win_lo;
     L.win_hi = m.win_hi;
@@ -204,8 +237,9 @@ __device__ __forceinline__ float4 table_at(const Lane &L, const float4 *__restri
     float u = fmaf(coord, SMEM ? M0.u_scale : L.u_scale, SMEM ? M0.u_shift : L.u_shift);
     u = fminf(fmaxf(u, -0.5f), SMEM ? M0.u_umax : L.u_max);
     const float t = u + kMagic;
-    const int i = __float_as_int(t) - 0x4b400000;
+    int i = __float_as_int(t) - 0x4b400000;
     f = u - (t - kMagic);
+    CHECK_INDEX(i, SMEM ? M0.M : L.M, kCheckTable);
     return SMEM ? tab[i] : __ldg(tab + L.tbase + i);
 }
 
@@ -236,8 +270,9 @@ __device__ __forceinline__ float drift_vpv(const Lane &L, const float4 *__restri
     if (u <= (SMEM ? M0.d_umax : L.dc.bump.umax)) {
         const float kMagic = 12582912.0f;                    // 1.5 * 2^23
         const float t = (u - 0.5f) + kMagic;
-        const int i = __float_as_int(t) - 0x4b400000;
+        int i = __float_as_int(t) - 0x4b400000;
         const float sv = u - (t - kMagic);
+        CHECK_INDEX(i, (int)(SMEM ? M0.d_umax : L.dc.bump.umax) + 1, kCheckDriftTable);
         const float4 c = SMEM ? tab[M0.dtab + i] : __ldg(tab + L.tbase + L.dc.bump.dtab + i);
         return fmaf(sv, fmaf(sv, fmaf(sv, c.w, c.z), c.y), c.x);
     }
@@ -266,6 +301,17 @@ __device__ __forceinline__ bool outside_window(const Lane &L, int n)
     return NIDX && L.nidx && (n < L.win_lo || n > L.win_hi);
 }
 
+// (pi^2/2 - 3) dN, the momentum drift's factor, as (0.5 dN pi) pi - 3 dN with
+// the FP32 constants 0.5 dN and -3 dN (single-model launches read them from
+// the model descriptor, the others form the same products from dN).
+template <bool SMEM>
+__device__ __forceinline__ float hh_dN(const Lane &L, const ModelDev &M0)
+{
+    const float h = SMEM ? M0.half_dN : 0.5f * L.dN;
+    const float m3 = SMEM ? M0.m3dN : -3.0f * L.dN;
+    return fmaf(h * L.p, L.p, m3);
+}
+
 // One Euler-Maruyama step of Eq. (4.7) with bias amplitude L.cb / sqrt(dN).
 // The field increment (drift + bias + noise) is formed first and added to the
 // compensated field pair: a plain FP32 field would add the same drift
@@ -290,15 +336,15 @@ __device__ __forceinline__ bool em_step(Lane &L, float z, const float4 *__restri
         half_cb2 = 0.0f;
     }
     const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model, M0);
-    const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
+    const float hdN = hh_dN<SMEM>(L, M0);               // (pi^2/2 - 3) dN
     const float zb = z + cb;                             // xi + alpha sqrt(dN)
     const float dx = fmaf(S, zb, L.p * dN);             // (pi + alpha S) dN + S xi sqrt(dN)
     if (DTAB) {
         // correlated pi-noise (tan theta_n ~ 0.3): the momentum is a compensated
         // pair, or its rounding performs a random walk that the field integrates
-        kahan_add(L.p, L.p_c, fmaf(T, zb, hh * dN * (L.p + vpv)));
+        kahan_add(L.p, L.p_c, fmaf(T, zb, hdN * (L.p + vpv)));
     } else {
-        L.p = fmaf(T, zb, fmaf(hh * dN, L.p + vpv, L.p));
+        L.p = fmaf(T, zb, fmaf(hdN, L.p + vpv, L.p));
     }
     if (WEIGHTED) L.lw_grp -= fmaf(cb, z, half_cb2);   // the step's ln w increment (see group_lw)
     kahan_add(L.x, L.x_c, dx);
@@ -485,6 +531,7 @@ __device__ __forceinline__ void refill_point(const EmParams &P, Lane &L, bool &a
     if (!fin) return;
     if (fin_me) {
         const bool pas = passed(L);
+        CHECK_INDEX(L.unit, P.total_units, kCheckUnit);
         P.nsteps[L.unit] = L.n;
         P.logw[L.unit] = (double)L.lw_hi - (double)L.lw_lo;     // the pair holds hi - lo
         P.status[L.unit] = pas ? (uint8_t)FPT_TRAJ_PASSED : (uint8_t)FPT_TRAJ_CAPPED;
@@ -688,8 +735,9 @@ __device__ __forceinline__ void table2_at(const Lane &L, const float4 *__restric
     float u = fmaf(L.x, SMEM ? M0.u_scale : L.u_scale, SMEM ? M0.u_shift : L.u_shift);
     u = fminf(fmaxf(u, 0.0f), SMEM ? M0.u_umax : L.u_max);
     const float t = (u - 0.5f) + kMagic;
-    const int i = __float_as_int(t) - 0x4b400000;
+    int i = __float_as_int(t) - 0x4b400000;
     const float f = u - (t - kMagic);
+    CHECK_INDEX(i, SMEM ? M0.M : L.M, kCheckTable);          // entries i, i + 1 of M + 1
     const float4 e0 = SMEM ? tab[i] : __ldg(tab + L.tbase + i);
     const float4 e1 = SMEM ? tab[i + 1] : __ldg(tab + L.tbase + i + 1);
     a = fmaf(f, e1.x - e0.x, e0.x);
@@ -705,12 +753,12 @@ __device__ __forceinline__ bool em2_step(Lane &L, float z1, float z2, const floa
     table2_at<SMEM>(L, tab, a, b, c, M0);
     const float vpv = drift_vpv<DTAB, SMEM>(L, tab, s_model, M0);
     const float dN = SMEM ? M0.dN : L.dN;
-    const float hh = fmaf(0.5f * L.p, L.p, -3.0f);      // pi^2/2 - 3
+    const float hdN = hh_dN<SMEM>(L, M0);               // (pi^2/2 - 3) dN
     const float e1 = z1 + L.cb, e2 = z2 + L.cb_b;       // xi + beta sqrt(dN)
     // (phi, pi) += D dN + S beta dN + S xi sqrt(dN) = D dN + (S sqrt(dN)) e
     const float dx = fmaf(a, e1, fmaf(b, e2, L.p * dN));
     // full-rank noise drives pi directly: compensated momentum (see em_step)
-    kahan_add(L.p, L.p_c, fmaf(b, e1, fmaf(c, e2, hh * dN * (L.p + vpv))));
+    kahan_add(L.p, L.p_c, fmaf(b, e1, fmaf(c, e2, hdN * (L.p + vpv))));
     if (WEIGHTED) L.lw_grp -= fmaf(L.cb, z1, fmaf(L.cb_b, z2, L.half_cb2));
     kahan_add(L.x, L.x_c, dx);
     ++L.n;
@@ -777,23 +825,69 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
 
         for (int g = 0; g < P.groups_per_check; ++g) {
             // four steps per group, two per Philox block: L.n is even at each block
-            // (a lane that finished keeps its count and ignores the normals). No
-            // fast path here: the 2-D step's bound (S_phiphi + |S_phipi|) is wide
-            // where the matched noise carries the decaying solution, and the
-            // measured rate fell with it (2.73e11 to 2.61e11 steps/s)
+            // (a lane that finished keeps its count and ignores the normals).
+            // Speculative group as in em_kernel: when every lane is live and four
+            // steps stay below the cap, they run without the per-step branch and a
+            // lane that passed at step k of the group is set back to the guarded
+            // path's state (k + 1 steps, the weight and noise sums of those steps
+            // formed again from the same normals, field marked passed).
+            if (SMEM && __all_sync(FULL, active && !done && L.n + 4 < P.m0.max_steps)) {
+                const float sx0 = REC ? sg.sum_xi : 0.0f, sy0 = REC ? sg.sum_xi2 : 0.0f;
+                bool hit[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 1, L.traj, L.run_id, 0u), P.rk);
-                float z[4];
-                box_muller(r.x, r.y, z[0], z[1]);
-                box_muller(r.z, r.w, z[2], z[3]);
-                if (active && !done) {
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 1, L.traj, L.run_id, 0u), P.rk);
+                    float z[4];
+                    box_muller(r.x, r.y, z[0], z[1]);
+                    box_muller(r.z, r.w, z[2], z[3]);
                     if (REC) { sg.sum_xi += z[0]; sg.sum_xi2 += z[1]; }
-                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model, P.m0);
-                }
-                if (active && !done) {
+                    em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model, P.m0);
+                    hit[2 * h] = passed(L);
                     if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
-                    done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
+                    em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
+                    hit[2 * h + 1] = passed(L);
+                }
+                if (hit[0] | hit[1] | hit[2] | hit[3]) {
+                    const int k = hit[0] ? 0 : hit[1] ? 1 : hit[2] ? 2 : 3;
+                    const int n0 = L.n - 4;
+                    float zz[8];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint4 r = philox4x32_10(make_uint4(((uint32_t)n0 >> 1) + h, L.traj, L.run_id, 0u),
+                                                      P.rk);
+                        box_muller(r.x, r.y, zz[4 * h], zz[4 * h + 1]);
+                        box_muller(r.z, r.w, zz[4 * h + 2], zz[4 * h + 3]);
+                    }
+                    float lw = 0.0f, sx = sx0, sy = sy0;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        if (s > k) break;
+                        lw -= fmaf(L.cb, zz[2 * s], fmaf(L.cb_b, zz[2 * s + 1], L.half_cb2));   // as em2_step
+                        sx += zz[2 * s];
+                        sy += zz[2 * s + 1];
+                    }
+                    L.n = n0 + k + 1;
+                    if (WEIGHTED) L.lw_grp = lw;
+                    if (REC) { sg.sum_xi = sx; sg.sum_xi2 = sy; }
+                    L.x = -1.0f;
+                    L.x_c = 0.0f;
+                    done = true;
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 1, L.traj, L.run_id, 0u), P.rk);
+                    float z[4];
+                    box_muller(r.x, r.y, z[0], z[1]);
+                    box_muller(r.z, r.w, z[2], z[3]);
+                    if (active && !done) {
+                        if (REC) { sg.sum_xi += z[0]; sg.sum_xi2 += z[1]; }
+                        done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model, P.m0);
+                    }
+                    if (active && !done) {
+                        if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
+                        done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
+                    }
                 }
             }
             if (WEIGHTED && L.lw_grp != 0.0f) {
@@ -914,7 +1008,11 @@ __global__ void hist_max_kernel(const HistParams P)
         double N;
         const double q = bin_coord(P.nsteps[u], P.dN, P.N_lo, P.db, N);
         const unsigned long long k = dkey(lw);
-        if (q >= 0.0 && q < (double)nb) atomicMax(&s_max[(int)floor(q)], k);
+        if (q >= 0.0 && q < (double)nb) {
+            int b = (int)floor(q);
+            CHECK_INDEX(b, nb, kCheckBin);
+            atomicMax(&s_max[b], k);
+        }
         atomicMax(&s_max[nb], k);
         if (has_tail && N >= P.N_tail) atomicMax(&s_max[nb + 1], k);
     }
@@ -985,8 +1083,9 @@ __global__ void hist_sum_kernel(const HistParams P)
             sc[kScTailN] += 1.0;
         }
         if (q < 0.0) { sc[kScUnder] += 1.0; continue; }
-        if (q >= (double)nb) { sc[kScOver] += 1.0; continue; }
-        const int b = (int)floor(q);
+        if (!(q < (double)nb)) { sc[kScOver] += 1.0; continue; }
+        int b = (int)floor(q);
+        CHECK_INDEX(b, nb, kCheckBin);
         const double e = exp(lw - s_M[b]);
         atomicAdd(&s_cnt[b], 1u);
         atomicAdd(&s_mom[4 * b], e);

@@ -156,6 +156,8 @@ _SIGNATURES = {
     "fpt_histogram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                         C.c_double, C.c_double, C.c_int32, C.c_double, C.c_void_p,
                                         C.c_void_p]),
+    "fpt_set_memory_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "fpt_memory_in_use": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "fpt_destroy": (None, [C.c_void_p]),
     "fpt_last_error": (C.c_char_p, [C.c_void_p]),
     "fpt_version": (C.c_char_p, []),
@@ -165,7 +167,9 @@ _LIB = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libfpt.so, or the bounds-checked debug build libfpt_checks.so when the
+    environment sets FPT_CHECKS=1 (built by build.build(checks=True))."""
+    return _build.LIB_CHECKS if os.environ.get("FPT_CHECKS", "") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -174,7 +178,7 @@ def load(build_if_missing: bool = False):
     if _LIB is not None:
         return _LIB
     if build_if_missing:
-        _build.build()
+        _build.build(checks=os.environ.get("FPT_CHECKS", "") == "1")
     path = library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first "
@@ -386,6 +390,19 @@ def fpt_get_launch(ctx: Context) -> dict:
     _check(load().fpt_get_launch(ctx.handle, C.byref(l)), ctx.handle)
     return dict(block=l.block, blocks_per_sm=l.blocks_per_sm, check_steps=l.check_steps,
                 use_graph=bool(l.use_graph), deadline_s=l.deadline_s)
+
+
+def fpt_set_memory_limit(ctx: Context, max_bytes: int) -> None:
+    """Cap the device memory the context may hold (0: no cap); allocations past
+    it fail with FPT_E_NOMEM and leave the context usable."""
+    _check(load().fpt_set_memory_limit(ctx.handle, int(max_bytes)), ctx.handle)
+
+
+def fpt_memory_in_use(ctx: Context) -> tuple:
+    """(bytes of device memory the context holds, its cap or 0)."""
+    used, cap = C.c_int64(0), C.c_int64(0)
+    _check(load().fpt_memory_in_use(ctx.handle, C.byref(used), C.byref(cap)), ctx.handle)
+    return used.value, cap.value
 
 
 def fpt_autotune(ctx: Context, runs: Sequence[fpt_run_desc], fraction: float = 0.25) -> dict:

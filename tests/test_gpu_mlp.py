@@ -279,3 +279,25 @@ def test_batch_training_equals_single_runs(torch):
                 assert st["loss"] == pytest.approx(hist[0][k]["loss"], rel=1e-12), (r, k)
                 assert np.array_equal(alones[k].params.cpu().numpy().view(np.uint32), got[k].view(np.uint32)), (r, k)
     assert not np.array_equal(got[0], got[2])
+
+
+def test_records_with_a_deadline_are_unaffected(torch):
+    """A launch with a deadline keeps its clock origin in its own flag words:
+    a record-mode run under a (generous) deadline returns the same records
+    and outputs as one without, and no record-overflow error."""
+    v, p = rand_params(11, out_scale=0.3)
+    n = 512
+    with bm_ctx() as ctx:
+        prop = TR.new_proposal(ctx, v, shift=(0, 0, 0), scale=(20.0, 100.0, 0.2), segment=64, alpha_max=2.0)
+        ref = fpt.fpt_run_records(ctx, prop.desc(0, n, seed=21, run_id=0), cap=1 << 16)
+        fpt.fpt_set_launch(ctx, deadline_s=60.0)
+        rec = fpt.fpt_run_records(ctx, prop.desc(0, n, seed=21, run_id=0), cap=1 << 16)
+        st, g = gpu_run(ctx, [prop.desc(0, n, seed=21, run_id=0)], [n])
+        assert st == fpt.FPT_OK
+        fpt.fpt_set_launch(ctx, deadline_s=0.0)
+        st, g0 = gpu_run(ctx, [prop.desc(0, n, seed=21, run_id=0)], [n])
+    assert rec["n_records"] == ref["n_records"] > 0
+    for k in ("in", "raw", "sum_xi", "unit", "n0"):
+        assert np.array_equal(rec[k], ref[k]), k
+    for k in ("nsteps", "logw", "status"):
+        assert np.array_equal(g[0][k], g0[0][k]), k

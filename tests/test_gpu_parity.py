@@ -302,3 +302,40 @@ def test_invalid_runs_are_rejected_before_launch(torch):
             assert e.value.status == fpt.FPT_E_INVALID
         with pytest.raises(fpt.FptError):
             fpt.fpt_histogram(ctx, 0, 1.0, 0.0, 8)
+
+
+def test_capped_allocator_reports_nomem_and_context_recovers(torch):
+    """The context's device allocations are counted; past its limit an
+    allocation fails as an out-of-memory cudaMalloc would: FPT_E_NOMEM, the
+    message names the limit, and the same context runs normally once the
+    request fits -- with the same trajectories as an uncapped context."""
+    wl = W.BM
+    S, Tt, lo, hi = bm_table()
+    n, small_n, spare = 1 << 20, 4096, 2 << 20
+    with fpt.fpt_init_model([wl.model]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, 16, 1.0, lo, hi, S, Tt)
+        used, cap = fpt.fpt_memory_in_use(ctx)
+        assert used > 0 and cap == 0
+        # 2^20 trajectories need ~21 MB of outputs; the 2^16-unit minimum fits in 1.4 MB
+        fpt.fpt_set_memory_limit(ctx, used + spare)
+        assert fpt.fpt_memory_in_use(ctx)[1] == used + spare
+        with pytest.raises(fpt.FptError) as e:
+            gpu_run(ctx, [fpt.run_desc(0, n, seed=3)], [n])
+        assert e.value.status == fpt.FPT_E_NOMEM and "limit" in str(e.value)
+        assert fpt.fpt_memory_in_use(ctx)[0] <= used + spare
+        st, small = gpu_run(ctx, [fpt.run_desc(0, small_n, seed=3)], [small_n])
+        assert st == fpt.FPT_OK
+        assert fpt.fpt_memory_in_use(ctx)[0] <= used + spare
+        with pytest.raises(fpt.FptError) as e:
+            fpt.fpt_set_memory_limit(ctx, -1)
+        assert e.value.status == fpt.FPT_E_INVALID
+        fpt.fpt_set_memory_limit(ctx, 0)
+        st, g = gpu_run(ctx, [fpt.run_desc(0, n, seed=3)], [n])
+        assert st == fpt.FPT_OK
+        assert fpt.fpt_memory_in_use(ctx)[0] > used + spare
+    with fpt.fpt_init_model([wl.model]) as ref:
+        fpt.fpt_noise_table(ref, 0, fpt.FPT_TABLE_USER, 16, 1.0, lo, hi, S, Tt)
+        st, r = gpu_run(ref, [fpt.run_desc(0, n, seed=3)], [n])
+    for k in ("nsteps", "logw", "status"):
+        assert np.array_equal(g[0][k], r[0][k])
+        assert np.array_equal(small[0][k], r[0][k][:small_n])

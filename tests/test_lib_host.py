@@ -46,6 +46,20 @@ def test_exports_every_declared_symbol():
     assert set(fpt._SIGNATURES) == set(names)
 
 
+def test_checked_build_compiles_and_loads():
+    """The FPT_CHECKS debug build (device bounds checks on table indexes,
+    trajectory indexes and histogram bins) compiles, loads beside the plain
+    build and exports the same functions."""
+    path = B.build(checks=True)
+    assert path == B.LIB_CHECKS != B.LIB
+    lib = C.CDLL(path)
+    lib.fpt_version.restype = C.c_char_p
+    assert b"FPT_CHECKS" in lib.fpt_version()
+    assert b"FPT_CHECKS" not in fpt.load().fpt_version()
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
 @pytest.mark.parametrize("wl", [W.LINEAR, W.BM])
 def test_resolve_explicit_models(wl):
     info = fpt.fpt_resolve_model(wl.model)
