@@ -339,3 +339,39 @@ def test_capped_allocator_reports_nomem_and_context_recovers(torch):
     for k in ("nsteps", "logw", "status"):
         assert np.array_equal(g[0][k], r[0][k])
         assert np.array_equal(small[0][k], r[0][k][:small_n])
+
+
+def test_pooled_runs_equal_one_histogram_of_their_union(torch, tmp_path):
+    """A sampling job of three runs (Philox run ids 0-2) pooled run by run
+    (paper_2410_13683_gb300.accumulate), checkpointed after the second and
+    resumed from the file, equals the library's histogram of the three runs'
+    trajectories taken in one call."""
+    from paper_2410_13683_gb300.accumulate import RunAccumulator
+    wl = W.BM
+    S, Tt, lo, hi = bm_table()
+    n, A, N_lo, N_hi, nb, N_tail = 1 << 16, 0.7, 0.0, 12.0, 256, 5.5
+    path = str(tmp_path / "job.npz")
+    outs = []
+    with fpt.fpt_init_model([wl.model]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, 16, 1.0, lo, hi, S, Tt)
+        acc = RunAccumulator(seed=9, N_lo=N_lo, N_hi=N_hi, n_bins=nb, N_tail=N_tail)
+        for r in range(3):
+            st, g = gpu_run(ctx, [fpt.run_desc(0, n, seed=9, run_id=r, A=A)], [n])
+            assert st == fpt.FPT_OK
+            outs.append(g[0])
+            acc.add(r, fpt.fpt_histogram(ctx, 0, N_lo, N_hi, nb, N_tail=N_tail))
+            if r == 1:
+                acc.save(path)
+                acc = RunAccumulator.load(path)
+        cat = {k: np.concatenate([o[k] for o in outs]) for k in ("nsteps", "logw", "status")}
+        h = fpt.fpt_histogram_data(ctx, cat["nsteps"], cat["logw"], cat["status"], wl.model.dN, N_lo, N_hi, nb,
+                                   N_tail=N_tail)
+    est = acc.estimates()
+    assert est["runs"] == 3 and est["n_total"] == h["n_total"] == 3 * n
+    assert np.array_equal(est["count"], h["count"])
+    np.testing.assert_allclose(est["pdf"], h["pdf"], rtol=1e-12)
+    np.testing.assert_allclose(est["se_w"], h["se_w"], rtol=1e-8, atol=1e-12 * np.max(h["se_w"]))
+    np.testing.assert_allclose(est["pdf_ln"], h["pdf_ln"], rtol=1e-11, equal_nan=True)
+    np.testing.assert_allclose(est["se_ln"], h["se_ln"], rtol=1e-11, equal_nan=True)
+    assert est["p_tail"] == pytest.approx(h["p_tail"], rel=1e-12)
+    assert est["ess_tail"] == pytest.approx(h["ess_tail"], rel=1e-11)
