@@ -103,6 +103,12 @@ __device__ __forceinline__ float uniform23(uint32_t r)
     return __int_as_float(0x3f800000u | (r >> 9)) - 0.99999994039535522f;   // 1 - 2^-24
 }
 
+// The normals are products (rho cos, rho sin): the record mode's sums of
+// normals are explicit __fadd_rn, which the compiler never fuses with the
+// product into an FMA. A contracted sum would round differently wherever the
+// compiler chose to fuse, and the speculative and guarded paths (and the
+// recomputation of a group's normals after a passage) would no longer give the
+// same sums.
 __device__ __forceinline__ void box_muller(uint32_t r0, uint32_t r1, float &z0, float &z1)
 {
     const float u0 = uniform23(r0);
@@ -662,7 +668,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
                 bool h[4];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    if (REC) sg.sum_xi += z[s];
+                    if (REC) sg.sum_xi = __fadd_rn(sg.sum_xi, z[s]);
                     em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                     h[s] = passed(L);
                 }
@@ -680,7 +686,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
                         float sx = sx0;
 #pragma unroll
                         for (int s = 0; s < 4; ++s)
-                            if (s <= k) sx += zz[s];
+                            if (s <= k) sx = __fadd_rn(sx, zz[s]);
                         sg.sum_xi = sx;
                     }
                     L.x = -1.0f;
@@ -691,7 +697,7 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
                     if (active && !done) {
-                        if (REC) sg.sum_xi += z[s];
+                        if (REC) sg.sum_xi = __fadd_rn(sg.sum_xi, z[s]);
                         done = em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                     }
             }
@@ -840,10 +846,10 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
                     float z[4];
                     box_muller(r.x, r.y, z[0], z[1]);
                     box_muller(r.z, r.w, z[2], z[3]);
-                    if (REC) { sg.sum_xi += z[0]; sg.sum_xi2 += z[1]; }
+                    if (REC) { sg.sum_xi = __fadd_rn(sg.sum_xi, z[0]); sg.sum_xi2 = __fadd_rn(sg.sum_xi2, z[1]); }
                     em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model, P.m0);
                     hit[2 * h] = passed(L);
-                    if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
+                    if (REC) { sg.sum_xi = __fadd_rn(sg.sum_xi, z[2]); sg.sum_xi2 = __fadd_rn(sg.sum_xi2, z[3]); }
                     em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
                     hit[2 * h + 1] = passed(L);
                 }
@@ -863,8 +869,8 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
                     for (int s = 0; s < 4; ++s) {
                         if (s > k) break;
                         lw -= fmaf(L.cb, zz[2 * s], fmaf(L.cb_b, zz[2 * s + 1], L.half_cb2));   // as em2_step
-                        sx += zz[2 * s];
-                        sy += zz[2 * s + 1];
+                        sx = __fadd_rn(sx, zz[2 * s]);
+                        sy = __fadd_rn(sy, zz[2 * s + 1]);
                     }
                     L.n = n0 + k + 1;
                     if (WEIGHTED) L.lw_grp = lw;
@@ -881,11 +887,11 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
                     box_muller(r.x, r.y, z[0], z[1]);
                     box_muller(r.z, r.w, z[2], z[3]);
                     if (active && !done) {
-                        if (REC) { sg.sum_xi += z[0]; sg.sum_xi2 += z[1]; }
+                        if (REC) { sg.sum_xi = __fadd_rn(sg.sum_xi, z[0]); sg.sum_xi2 = __fadd_rn(sg.sum_xi2, z[1]); }
                         done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[0], z[1], tab, s_model, P.m0);
                     }
                     if (active && !done) {
-                        if (REC) { sg.sum_xi += z[2]; sg.sum_xi2 += z[3]; }
+                        if (REC) { sg.sum_xi = __fadd_rn(sg.sum_xi, z[2]); sg.sum_xi2 = __fadd_rn(sg.sum_xi2, z[3]); }
                         done = em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
                     }
                 }
