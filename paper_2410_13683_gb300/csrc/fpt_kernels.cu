@@ -633,7 +633,6 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
     stage_launch<SMEM, MLP && !MNET>(P, s_tab, s_run, s_model, s_t0, s_tiles);
 
     const float4 *tab = SMEM ? s_tab : P.tables;
-    const unsigned lane = threadIdx.x & 31u;
     const unsigned FULL = 0xffffffffu;
 
     Lane L;
