@@ -732,6 +732,31 @@ def bump_leg(fpt, torch, shard, stream, seed, rank, sm_count, sm_max, autotune=T
     return out
 
 
+def legs_once(fpt, torch, n=1 << 22, seed=17):
+    """One direct launch (no bias, default launch shape) of each constant-bias
+    stepper variant at the legs' sizes -- the 1-D stepper on the sudden-
+    transition model's Bessel table, the full-rank 2-D stepper on its numerical
+    table, the noise-window stepper on the time-indexed table, the bump stepper
+    with its drift table -- for profiling them under ncu (one launch each, in
+    this order); prints the EM steps of each launch as one JSON line."""
+    m = usr_model()
+    cases = [("direct", m, lambda c: fpt.fpt_noise_table(c, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0)),
+             ("noise_2d", m, lambda c: fpt.fpt_noise_table2(c, 0, fpt.FPT_TABLE_NUMERIC, 4096, 1.0)),
+             ("window", m, lambda c: fpt.fpt_noise_table(c, 0, fpt.FPT_TABLE_BESSEL_N, 4096, 1.0, 0.0,
+                                                        m.n_end - m.n_in)),
+             ("bump", W.BUMP_MODEL, lambda c: fpt.fpt_noise_table(c, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0))]
+    out = {}
+    for name, mod, table in cases:
+        with fpt.fpt_init_model([mod], device=torch.cuda.current_device()) as ctx:
+            table(ctx)
+            st = fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=seed)])
+            fpt.fpt_sync(ctx)
+            h = fpt.fpt_histogram(ctx, 0, 0.0, 100.0, 512)
+            steps = passed_steps(h, mod.dN) + h["n_capped"] * float(mod.max_steps)
+            out[name] = {"em_steps": steps, "status": int(st)}
+    print(json.dumps({"legs_once": out, "n_traj": n}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -756,6 +781,8 @@ def main():
     ap.add_argument("--pipeline", type=int, default=2, help="steps in flight (contexts / streams)")
     ap.add_argument("--net", default="", help="load a trained proposal (.npz of --save-net) instead of training")
     ap.add_argument("--save-net", default="", help="store the trained proposal (.npz)")
+    ap.add_argument("--legs-once", action="store_true",
+                    help="profiling aid: one direct launch of each constant-bias stepper variant, then exit")
     args = ap.parse_args()
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -773,6 +800,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     __graft_entry__.build()
+    if args.legs_once:
+        return legs_once(fpt, torch)
     TRAIN["rounds"] = args.train_rounds
     TRAIN["lam"] = args.lam
     tail = load_tail()
