@@ -76,3 +76,45 @@ def test_gpu_tail_matches_inverse_gaussian(torch, p):
 
     pg, po = tail_p(g[0]["nsteps"], g[0]["logw"]), tail_p(o.nsteps, o.logw)
     assert pg == pytest.approx(po, rel=2e-3)
+
+
+def test_gpu_direct_law_is_the_shifted_inverse_gaussian(torch):
+    """The bulk of the GPU's first-passage law against the closed form, not
+    through the oracle: 2^22 direct paths of the exponential model binned per
+    50 steps over [3.5, 6.5] e-folds. A path with n > k steps stayed above the
+    end surface at steps 1..k, so P(n > k) = IG_sf(k dN) with the shifted
+    barrier (Siegmund), and a bin (k1, k2] holds IG_sf(k1 dN) - IG_sf(k2 dN)
+    of the paths. The counts must pass a chi-square test against that law and
+    fail it against the continuous-monitoring law; the mean must match Wald's
+    identity with the Siegmund overshoot (to its first drift correction)."""
+    from scipy import stats as sst
+    m = W.BM.model
+    n = 1 << 22
+    S, T = np.full(16, W.BM_S), np.zeros(16)
+    with fpt.fpt_init_model([m]) as ctx:
+        fpt.fpt_noise_table(ctx, 0, fpt.FPT_TABLE_USER, 16, 1.0, -0.1, 0.2, S, T)
+        st, g = gpu_run(ctx, [fpt.run_desc(0, n, seed=151, run_id=0)], [n])
+    assert st == fpt.FPT_OK and np.all(g[0]["status"] == fpt.FPT_TRAJ_PASSED)
+    k = g[0]["nsteps"].astype(np.int64)
+    edges = np.arange(3500, 6501, 50)
+    obs = np.array([np.sum((k > a) & (k <= b)) for a, b in zip(edges[:-1], edges[1:])], np.float64)
+
+    def chi2_p(law):
+        sf = law.sf(edges * m.dN)
+        exp = n * (sf[:-1] - sf[1:])
+        keep = exp >= 50
+        c2 = float(np.sum((obs[keep] - exp[keep]) ** 2 / exp[keep]))
+        return c2, float(sst.chi2.sf(c2, int(keep.sum()) - 1)), int(keep.sum())
+
+    d, mean, lam = ig_law()
+    c2, p, nb = chi2_p(d)
+    d0, _, _ = ig_law(shift=False)
+    c20, p0, _ = chi2_p(d0)
+    print(f"chi2 {c2:.1f} over {nb} bins (p = {p:.3g}); continuous monitoring: chi2 {c20:.1f} (p = {p0:.3g})")
+    assert p > 1e-3
+    assert p0 < 1e-6
+    # Wald: mu E[N] = a + E[overshoot]; the overshoot is 0.5826 s sqrt(dN) in the
+    # limit of a small drift per step, which here is theta = mu sqrt(dN)/s = 0.32 of the
+    # step's noise: the first correction, ~theta/4 of s sqrt(dN), moves E[N] by ~2.5e-4
+    N = k * m.dN
+    assert abs(N.mean() - mean) < 4.0 * N.std() / math.sqrt(n) + 5e-4
