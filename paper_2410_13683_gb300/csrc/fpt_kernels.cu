@@ -647,22 +647,25 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
             else mlp_segment_start<SMEM, REC>(L, active && L.mlp, sg, tab, s_tiles, s_bias, prun, P.m0);
         }
 
+        // Speculative groups (single-model launches): when every lane of the
+        // warp is live and the whole interval stays below the cap, the four steps
+        // of a group run without the per-step branch, each lane noting after
+        // which steps its field was at or below the end surface. A lane that
+        // passed at step k of the group then takes the state the guarded path
+        // would have left: k + 1 steps counted, the ln w increments of those
+        // steps summed again from the same operands, its field marked passed
+        // (the later steps' field and momentum are discarded: the trajectory has
+        // ended, and only its step count, weight and status are kept), and the
+        // warp's remaining groups of the interval run guarded. Results do not
+        // depend on which path ran.
+        bool spec = SMEM && __all_sync(FULL, active && !done &&
+                                                 L.n + 4 * P.groups_per_check < P.m0.max_steps);
         for (int g = 0; g < P.groups_per_check; ++g) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)L.n >> 2, L.traj, L.run_id, 0u), P.rk);
             float z[4];
             box_muller(r.x, r.y, z[0], z[1]);
             box_muller(r.z, r.w, z[2], z[3]);
-            // Speculative group (single-model launches): when every lane of the
-            // warp is live and four steps stay below the cap, the four steps run
-            // without the per-step branch, each lane noting after which steps its
-            // field was at or below the end surface. A lane that passed at step k
-            // of the group then takes the state the guarded path would have left:
-            // k + 1 steps counted, the ln w increments of those steps summed again
-            // from the same operands, its field marked passed (the later steps'
-            // field and momentum are discarded: the trajectory has ended, and only
-            // its step count, weight and status are kept). Results do not depend
-            // on which path ran.
-            if (SMEM && __all_sync(FULL, active && !done && L.n + 4 < P.m0.max_steps)) {
+            if (spec) {
                 const float sx0 = REC ? sg.sum_xi : 0.0f;
                 bool h[4];
 #pragma unroll
@@ -671,7 +674,9 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, (MLP || NIDX || DTAB
                     em_step<WEIGHTED, SMEM, NIDX, DTAB>(L, z[s], tab, s_model, P.m0);
                     h[s] = passed(L);
                 }
-                if (h[0] | h[1] | h[2] | h[3]) {
+                const bool hit = h[0] | h[1] | h[2] | h[3];
+                if (__any_sync(FULL, hit)) spec = false;
+                if (hit) {
                     const int k = h[0] ? 0 : h[1] ? 1 : h[2] ? 2 : 3;
                     const int n0 = L.n - 4;
                     // the group's normals again (not kept live through the steps)
