@@ -738,7 +738,8 @@ def legs_once(fpt, torch, n=1 << 22, seed=17):
     transition model's Bessel table, the full-rank 2-D stepper on its numerical
     table, the noise-window stepper on the time-indexed table, the bump stepper
     with its drift table -- for profiling them under ncu (one launch each, in
-    this order); prints the EM steps of each launch as one JSON line."""
+    this order, after one warm-up launch each); prints the EM steps and the
+    CUDA-event time of each timed launch as one JSON line."""
     m = usr_model()
     cases = [("direct", m, lambda c: fpt.fpt_noise_table(c, 0, fpt.FPT_TABLE_BESSEL, 4096, 1.0)),
              ("noise_2d", m, lambda c: fpt.fpt_noise_table2(c, 0, fpt.FPT_TABLE_NUMERIC, 4096, 1.0)),
@@ -749,11 +750,18 @@ def legs_once(fpt, torch, n=1 << 22, seed=17):
     for name, mod, table in cases:
         with fpt.fpt_init_model([mod], device=torch.cuda.current_device()) as ctx:
             table(ctx)
-            st = fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=seed)])
-            fpt.fpt_sync(ctx)
-            h = fpt.fpt_histogram(ctx, 0, 0.0, 100.0, 512)
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=seed + 1)], stream=stream)    # warm-up (graph capture)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = fpt.fpt_run(ctx, [fpt.run_desc(0, n, seed=seed)], stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            h = fpt.fpt_histogram(ctx, 0, 0.0, 100.0, 512, stream=stream)
             steps = passed_steps(h, mod.dN) + h["n_capped"] * float(mod.max_steps)
-            out[name] = {"em_steps": steps, "status": int(st)}
+            ms = e0.elapsed_time(e1)
+            out[name] = {"em_steps": steps, "ms": ms, "em_steps_per_s": steps / (ms * 1e-3), "status": int(st)}
     print(json.dumps({"legs_once": out, "n_traj": n}))
 
 

@@ -833,15 +833,18 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
         if (MLP && __any_sync(FULL, active && L.mlp))
             mlp2_segment_start<SMEM, REC>(L, active && L.mlp, sg, s_tiles, s_bias, prun, P.m0);
 
+        // speculative groups as in em_kernel, the precondition checked once per interval
+        bool spec = SMEM && __all_sync(FULL, active && !done &&
+                                                 L.n + 4 * P.groups_per_check < P.m0.max_steps);
         for (int g = 0; g < P.groups_per_check; ++g) {
             // four steps per group, two per Philox block: L.n is even at each block
             // (a lane that finished keeps its count and ignores the normals).
-            // Speculative group as in em_kernel: when every lane is live and four
-            // steps stay below the cap, they run without the per-step branch and a
-            // lane that passed at step k of the group is set back to the guarded
-            // path's state (k + 1 steps, the weight and noise sums of those steps
-            // formed again from the same normals, field marked passed).
-            if (SMEM && __all_sync(FULL, active && !done && L.n + 4 < P.m0.max_steps)) {
+            // Speculative group as in em_kernel: when every lane is live and the
+            // interval stays below the cap, the steps run without the per-step
+            // branch and a lane that passed at step k of the group is set back to
+            // the guarded path's state (k + 1 steps, the weight and noise sums of
+            // those steps formed again from the same normals, field marked passed).
+            if (spec) {
                 const float sx0 = REC ? sg.sum_xi : 0.0f, sy0 = REC ? sg.sum_xi2 : 0.0f;
                 bool hit[4];
 #pragma unroll
@@ -857,7 +860,9 @@ __global__ void __launch_bounds__(MLP ? kMlpMaxBlock : 512, 2) em2_kernel(const 
                     em2_step<WEIGHTED, SMEM, DTAB>(L, z[2], z[3], tab, s_model, P.m0);
                     hit[2 * h + 1] = passed(L);
                 }
-                if (hit[0] | hit[1] | hit[2] | hit[3]) {
+                const bool any_hit = hit[0] | hit[1] | hit[2] | hit[3];
+                if (__any_sync(FULL, any_hit)) spec = false;
+                if (any_hit) {
                     const int k = hit[0] ? 0 : hit[1] ? 1 : hit[2] ? 2 : 3;
                     const int n0 = L.n - 4;
                     float zz[8];
