@@ -1,6 +1,7 @@
 """Host arithmetic of bench.py on CPU: the clock-record parser (throttle
 reasons decide whether a number stands), the issue roofline, the step count
-of runs where no path passed, and the constant-amplitude sweep's pick."""
+of runs where no path passed, the constant-amplitude sweep's pick, the ESS
+spread, and the reference arm's JSON line."""
 import math
 
 import numpy as np
@@ -96,3 +97,23 @@ def test_ess_spread_covers_the_repeat_to_repeat_scatter():
     sw2[3] = 50.0
     r = shard.ess_spread(sw, sw2)
     assert r["lo"] < 0.5 and r["hi"] > 1.2
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one
+    JSON line with the contract's keys, on a small sample."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+                        "--ref-traj", "2048"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "dtype", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
