@@ -143,16 +143,17 @@ def train_select(ctx, prop: Proposal, model: int, rounds: int, checkpoints, val_
 
 
 def new_proposals(ctx, init_params, shifts, scales, segment: int = 64, alpha_max: float = 4.0, flags: int = 0,
-                  x_floors=None):
+                  x_floors=None, device: str = "cuda"):
     """len(init_params) proposals whose parameters and packed blobs are the
     rows of two shared device tensors, as fpt_mlp_train_batch expects."""
     import torch
     n = len(init_params)
-    P = torch.tensor(np.stack([np.asarray(v, np.float32) for v in init_params]), device="cuda")
-    B = torch.zeros((n, fpt.FPT_MLP_BLOB_BYTES), dtype=torch.uint8, device="cuda")
+    P = torch.tensor(np.stack([np.asarray(v, np.float32) for v in init_params]), device=device)
+    B = torch.zeros((n, fpt.FPT_MLP_BLOB_BYTES), dtype=torch.uint8, device=device)
     for k in range(n):
         fpt.fpt_mlp_pack(ctx, P[k], B[k])
-    torch.cuda.synchronize()
+    if P.is_cuda:
+        torch.cuda.synchronize()
     fl = list(x_floors) if x_floors is not None else [0.0] * n
     props = [Proposal(P[k], B[k], tuple(float(v) for v in shifts[k]), tuple(float(v) for v in scales[k]), segment,
                       alpha_max, flags, float(fl[k])) for k in range(n)]
@@ -223,3 +224,34 @@ def load_checkpoint(ctx, path: str, device: str = "cuda") -> Proposal:
     prop._adam = (torch.tensor(z["adam_m"], device=dev), torch.tensor(z["adam_v"], device=dev))
     prop.history = json.loads(str(z["history"]))
     return prop
+
+
+def save_batch_checkpoint(props, P, path: str) -> None:
+    """The state of a batch training (train_batch): every proposal's fp32
+    parameters (the rows of P), the shared Adam moments, each proposal's input
+    normalisation and history (the next round number is len(history))."""
+    import json
+    import torch
+    m, v = getattr(P, "_adam", (torch.zeros_like(P), torch.zeros_like(P)))
+    meta = [dict(shift=list(q.shift), scale=list(q.scale), segment=q.segment, alpha_max=q.alpha_max, flags=q.flags,
+                 x_floor=q.x_floor, history=q.history) for q in props]
+    np.savez(path, params=P.detach().cpu().numpy(), adam_m=m.detach().cpu().numpy(),
+             adam_v=v.detach().cpu().numpy(), meta=json.dumps(meta))
+
+
+def load_batch_checkpoint(ctx, path: str, device: str = "cuda"):
+    """(props, P, B) of a batch training saved by save_batch_checkpoint, packed
+    for ctx, with the Adam moments restored: train_batch(..., first_round=
+    len(props[0].history)) continues it as if it had not stopped."""
+    import json
+    import torch
+    z = np.load(path)
+    meta = json.loads(str(z["meta"]))
+    q0 = meta[0]
+    props, P, B = new_proposals(ctx, list(z["params"]), [q["shift"] for q in meta], [q["scale"] for q in meta],
+                                segment=q0["segment"], alpha_max=q0["alpha_max"], flags=q0["flags"],
+                                x_floors=[q["x_floor"] for q in meta], device=device)
+    P._adam = (torch.tensor(z["adam_m"], device=P.device), torch.tensor(z["adam_v"], device=P.device))
+    for q, mq in zip(props, meta):
+        q.history = mq["history"]
+    return props, P, B

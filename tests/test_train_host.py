@@ -149,3 +149,40 @@ def test_checkpoint_resume_equals_uninterrupted_training(monkeypatch, tmp_path):
     assert [h["round"] for h in b.history] == [h["round"] for h in ref.history]
     assert torch.equal(b.params, ref.params)
     assert all(torch.equal(x, y) for x, y in zip(b._adam, ref._adam))
+
+
+def test_batch_checkpoint_resume_equals_uninterrupted_training(monkeypatch, tmp_path):
+    """A batch training (every proposal of a model family in one call per
+    round) saved after 2 rounds and resumed for 2 more equals 4 rounds without
+    the stop: parameters, shared Adam moments, run ids and histories."""
+    def fake(ctx, runs, lam, cuts, adam, P, m, v, B, stream=None):
+        ids = torch.tensor([float(r.run_id) for r in runs])[:, None]
+        g = torch.cos(P * 0.7 + ids)
+        m.mul_(0.9).add_(0.1 * g)
+        v.mul_(0.999).add_(0.001 * g * g)
+        P.sub_(adam["lr"] * m / (v.sqrt() + 1e-8))
+        return [{"loss": float(P[k].sum()), "run_id": int(r.run_id)} for k, r in enumerate(runs)]
+
+    monkeypatch.setattr(fpt, "fpt_mlp_train_batch", fake)
+    monkeypatch.setattr(fpt, "fpt_mlp_pack", lambda ctx, p, b, stream=None: None)
+
+    def fresh():
+        return TR.new_proposals(None, [np.linspace(-1, 1, 8) * (k + 1) for k in range(3)],
+                                [(0.1 * k, 0.0, 0.0) for k in range(3)], [(0.2, 1.0 + k, 0.01) for k in range(3)],
+                                segment=128, alpha_max=8.0, flags=fpt.FPT_MLP_LOG_X,
+                                x_floors=[1e-4 * (k + 1) for k in range(3)], device="cpu")
+
+    kw = dict(models=[0, 1, 2], n_traj=512, seed=5, lam=0.25, N_cuts=[10.0, 20.0, 30.0])
+    props_r, P_r, B_r = fresh()
+    TR.train_batch(None, props_r, P_r, B_r, rounds=4, **kw)
+
+    props_a, P_a, B_a = fresh()
+    TR.train_batch(None, props_a, P_a, B_a, rounds=2, **kw)
+    path = str(tmp_path / "batch.npz")
+    TR.save_batch_checkpoint(props_a, P_a, path)
+    props_b, P_b, B_b = TR.load_batch_checkpoint(None, path, device="cpu")
+    assert [(q.shift, q.scale, q.x_floor) for q in props_b] == [(q.shift, q.scale, q.x_floor) for q in props_a]
+    TR.train_batch(None, props_b, P_b, B_b, rounds=2, first_round=len(props_b[0].history), **kw)
+    assert torch.equal(P_b, P_r)
+    assert all(torch.equal(x, y) for x, y in zip(P_b._adam, P_r._adam))
+    assert [h["run_id"] for h in props_b[1].history] == [h["run_id"] for h in props_r[1].history] == [1, 4, 7, 10]
